@@ -1,0 +1,316 @@
+"""Benchmark: two-phase lattice Boltzmann step with curved walls on the 4096^2 droplet-on-cylinder
+lattice, in million fluid-node updates per second (MLUPS) and as a fraction of the measured HBM
+roofline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One "step" is one time step of the whole hot path: the fused step kernel over every node plus the
+curved-wall pass over the boundary links.  The headline line times modified scheme B with FP32
+deviation storage; "variants" times the five boundary variants (MLS, L-Bouzidi, Zhao-Yong, A, B)
+in FP64 and FP32 deviation storage.  Under torchrun each rank advances its own replica of the
+lattice (weak scaling, no data-path collective); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline per GB300; served p50/p99 latency vs plain FP64"
+UNIT = "MLUPS"
+SCHEME_NAMES = ("mls", "bouzidi_l", "zhao_yong", "mod_a", "mod_b")
+
+
+def bytes_per_update(precision):
+    # algorithmic traffic of one fluid-node update: 9 populations read + 9 written
+    return 2 * 9 * (8 if precision == "fp64" else 4)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("LBM_BENCH_BACKEND", "nccl")
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    """Maximum of a float over ranks (identity for one process)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_lattice(w, scheme, precision):
+    from paper_1908_09235_gb300 import lbm
+    eos = lbm.make_eos(lbm.EOS_CS, **w.eos)
+    rl, rv = lbm.lbm_coexistence(eos)
+    eos.rho_wall = rv
+    lat = lbm.Lattice(w.nx, w.ny, w.tau, scheme, circles=w.circles, eos=eos,
+                      precision=precision, rho_ref=0.5 * (rl + rv))
+    lat.init_droplet(*w.drop, rl, rv)
+    return lat, (rl, rv)
+
+
+def time_variant(w, scheme, precision, steps, warmup):
+    """Timed region of one variant: CUDA events around every kernel on the library's stream."""
+    lat, _ = make_lattice(w, scheme, precision)
+    lat.step_timed(warmup)
+    ms_step, ms_bnd, ms_total = lat.step_timed(steps)
+    info = lat.info()
+    lat.close()
+    return ms_step, ms_bnd, ms_total, info
+
+
+def cpu_oracle_rate(w, budget_s, max_steps):
+    """The FP64 CPU oracle on the same lattice, one thread, as many steps as fit the budget."""
+    import oracle as O
+    c = w.eos
+    Tc, _ = O.cs_critical(c["a"], c["b"], c["R"])
+    rl, rv = O.cs_coexistence(c["a"], c["b"], c["R"], c["T_over_Tc"] * Tc)
+    s = O.OracleSim(w.nx, w.ny, w.tau, scheme=O.MOD_B, circles=w.circles, eos=O.EOS_CS, G=c["G"],
+                    a=c["a"], b=c["b"], R=c["R"], T_over_Tc=c["T_over_Tc"], rho_wall=rv)
+    s.init_droplet(*w.drop, rl, rv)
+    n_fluid = int((s.flags() & 1 == 0).sum())
+    done, t0 = 0, time.perf_counter()
+    while done < max_steps:
+        s.step(1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n_fluid * done / dt / 1e6, done, dt
+
+
+def run_reference(args, w):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    mlups, done, dt = cpu_oracle_rate(w, budget_s=max(10.0, 3.0 * args.steps), max_steps=args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": UNIT,
+            "n_gpus": 0, "steps": done, "warmup": 0, "ms_per_step": round(1e3 * dt / done, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "scheme": "mod_b"},
+            "cpu_baseline": {"value": round(mlups, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d FP64 time steps of the %dx%d lattice (%.1f s)"
+                                       % (done, w.nx, w.ny, dt)},
+            "e2e": {"value": round(mlups, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(w, steps):
+    """Same metric through the public API with host buffers: upload rho, u from pinned host memory,
+    run the steps, read rho, u back; all inside the timed region."""
+    import numpy as np
+    import torch
+
+    from paper_1908_09235_gb300 import lbm
+    lat, (rl, rv) = make_lattice(w, lbm.MOD_B, lbm.FP32_DEV)
+    n = w.nx * w.ny
+    host = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    rho, ux, uy = lat.fields()  # a realistic initial state (the droplet), staged in pinned memory
+    host[0].numpy()[:] = np.nan_to_num(rho.ravel(), nan=rv)
+    host[1].numpy()[:] = np.nan_to_num(ux.ravel())
+    host[2].numpy()[:] = np.nan_to_num(uy.ravel())
+    out = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    lib = lbm.load_library()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm._check(lat.ctx, lib.lbm_init_fields(lat.ctx, host[0].data_ptr(), host[1].data_ptr(),
+                                            host[2].data_ptr()))
+    lbm._check(lat.ctx, lib.lbm_step(lat.ctx, steps))
+    lbm._check(lat.ctx, lib.lbm_fields(lat.ctx, out[0].data_ptr(), out[1].data_ptr(),
+                                       out[2].data_ptr()))
+    dt = time.perf_counter() - t0
+    info = lat.info()
+    lat.close()
+    return info["n_fluid"] * steps / dt / 1e6, 24 * n / steps, 24 * n / steps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--variant-steps", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    from paper_1908_09235_gb300 import workloads
+    w = workloads.LARGE
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1908_09235_gb300 import lbm
+    lbm.load_library()
+
+    # ---- headline: scheme B, FP32 deviation storage ----
+    lat, _ = make_lattice(w, lbm.MOD_B, lbm.FP32_DEV)
+    lat.step_timed(args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    with Clocks(local) as clk:
+        ms_step, ms_bnd, ms_total = lat.step_timed(args.steps)
+    torch.cuda.synchronize()
+    barrier(world)
+    info = lat.info()
+    m_after = lat.mass()
+    lat.close()
+    ms_total = max_over_ranks(ms_total, world)
+    n_fluid, n_all = info["n_fluid"], w.nx * w.ny
+    value = world * n_fluid * args.steps / (ms_total * 1e-3) / 1e6
+    peak, peak_kind = measured_peaks()
+    bpu = bytes_per_update("fp32_dev")
+    achieved = n_fluid * bpu / (ms_step / args.steps * 1e-3) / 1e9
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = None
+    if os.path.exists(traffic_file):
+        with open(traffic_file) as f:
+            traffic = json.load(f).get("step_kernel_fp32_dev_4096")
+
+    variants = {}
+    for prec in ("fp64", "fp32_dev"):
+        for name in SCHEME_NAMES:
+            s_ms, b_ms, t_ms, vinfo = time_variant(w, lbm.SCHEMES[name], lbm.PRECISIONS[prec],
+                                                   args.variant_steps, 3)
+            vb = bytes_per_update(prec)
+            variants["%s/%s" % (prec, name)] = {
+                "mlups": round(n_fluid * args.variant_steps / (t_ms * 1e-3) / 1e6, 1),
+                "step_kernel_us": round(1e3 * s_ms / args.variant_steps, 2),
+                "boundary_kernel_us": round(1e3 * b_ms / args.variant_steps, 2),
+                "hbm_frac_step_kernel": round(
+                    n_fluid * vb / (s_ms / args.variant_steps * 1e-3) / 1e9 / peak, 3)}
+
+    e2e_value, h2d, d2h = run_e2e(w, args.steps)
+    e2e_value = world * e2e_value
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, done, dt = cpu_oracle_rate(w, budget_s=15.0, max_steps=50)
+        cpu = {"value": round(mlups, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d FP64 time steps of the %dx%d lattice, scheme B (%.1f s)"
+                         % (done, w.nx, w.ny, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_total / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "scheme": "mod_b", "storage": "fp32_dev",
+                       "nodes": n_all, "fluid_nodes": n_fluid,
+                       "boundary_links": info["n_links"],
+                       "l2": "inputs larger than L2 (two 604 MB lattices)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "mlups_all_nodes": round(world * n_all * args.steps / (ms_total * 1e-3) / 1e6, 1),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "step_kernel (fused force+collision+stream)",
+                         "bytes_per_fluid_update": bpu},
+            "step_kernel_us": round(1e3 * ms_step / args.steps, 2),
+            "boundary_kernel_us": round(1e3 * ms_bnd / args.steps, 2),
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1)},
+            "cpu_baseline": cpu,
+            "variants": variants,
+            "mass_after": m_after,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

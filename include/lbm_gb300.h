@@ -1,0 +1,196 @@
+/*
+ * lbm_gb300.h -- C ABI of the GB300 (sm_103a) two-phase lattice Boltzmann library.
+ *
+ * The library advances the D2Q9 pseudopotential lattice Boltzmann method with curved solid walls
+ * of Yu, Li & Wen, "Modified curved boundary scheme for two-phase lattice Boltzmann simulations"
+ * (arXiv:1908.09235).  One time step is
+ *   (i)  a fused pass over every fluid node: density and velocity (Eq. 5), the pseudopotential
+ *        interaction force of Eq. (16) from psi(rho) of the eight neighbours, BGK collision with
+ *        Guo forcing (Eqs. 1, 2, 4) and streaming (Eq. 3);
+ *  (ii)  a pass over the boundary nodes that sets the populations entering the fluid across the
+ *        curved wall, with the scheme chosen at creation: halfway bounce-back, Filippova-Haenel
+ *        (Eqs. 7-10), Mei-Luo-Shyy (Eqs. 7, 8, 10, 11), linear / quadratic Bouzidi (Eqs. 12, 13),
+ *        Zhao-Yong (Eq. 14), modified scheme A (Eqs. 15, 17, 18), modified scheme B
+ *        (Eqs. 19-22) or the fictitious density of Bao et al. (Eq. 23).
+ * Everything in (i) and (ii) runs in CUDA kernels on one GPU; the host only validates arguments,
+ * builds the Carnahan-Starling constants and copies fields in and out.
+ *
+ * Conventions.  Node (i, j) sits at position (i, j) in lattice units, i in [0, nx), j in [0, ny);
+ * its linear index is j*nx + i (row-major, y outer).  The outer box is periodic in x and y.
+ * D2Q9 directions: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ * All host arrays are caller-owned and are read or written only during the call.  Device state is
+ * owned by the context and released by lbm_destroy.  Functions return an lbm_status; a non-zero
+ * status is also recorded as the context's sticky error (lbm_last_error) and makes every later
+ * call on that context return the same status, except lbm_destroy and lbm_last_error.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,    /* invalid argument; nothing was changed                              */
+  LBM_ENOMEM = 2,    /* device allocation failed                                           */
+  LBM_ECUDA = 3,     /* a CUDA call failed (message in lbm_last_error)                     */
+  LBM_EUNSTABLE = 4, /* a density became non-positive or not finite (detected by lbm_mass) */
+  LBM_ETIMEOUT = 5,  /* a bounded device wait gave up                                      */
+  LBM_ESTATE = 6     /* call out of order (e.g. lbm_step before any initialisation)       */
+} lbm_status;
+
+/* Curved-wall scheme applied at every boundary link (Sec. 2.2 and Sec. 4.1). */
+typedef enum {
+  LBM_HBB = 0,        /* halfway bounce-back: f_abar(x_b, t+1) = f*_a(x_b, t)              */
+  LBM_FH = 1,         /* Filippova-Haenel, Eqs. (7)-(10); rejected when |tau - 1| < 1e-3   */
+  LBM_MLS = 2,        /* Mei-Luo-Shyy, Eqs. (7), (8), (10), (11)                          */
+  LBM_BOUZIDI_L = 3,  /* linear interpolated bounce-back, Eq. (12)                        */
+  LBM_BOUZIDI_Q = 4,  /* quadratic interpolated bounce-back, Eq. (13)                     */
+  LBM_ZHAO_YONG = 5,  /* single-node scheme, Eq. (14)                                     */
+  LBM_MOD_A = 6,      /* modified scheme A: MLS, then f_0(x_b) += leakage, Eqs. (15)-(18) */
+  LBM_MOD_B = 7,      /* modified scheme B: MLS with the fictitious density of Eq. (22)   */
+  LBM_BAO = 8,        /* MLS with the fictitious density of Eq. (23) (Bao et al.)         */
+  LBM_BOUZIDI_L_A = 9 /* linear Bouzidi, then the rest-population correction of Eq. (18)  */
+} lbm_scheme;
+
+/* How populations are stored in device memory.  Arithmetic is FP64 for LBM_FP64 and FP32 for
+ * the deviation formats, which store f_a - w_a rho_ref.  The boundary pass always computes in
+ * FP64; with deviation storage its rounding residue is carried per boundary node in FP64 so the
+ * mass-conserving schemes stay conserving. */
+typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 } lbm_precision;
+
+typedef enum { LBM_EOS_NONE = 0, LBM_EOS_EXP = 1, LBM_EOS_CS = 2 } lbm_eos_kind;
+
+typedef struct {
+  double cx, cy, r;      /* centre and radius in lattice units                                  */
+  int32_t solid_outside; /* 0: nodes with |x - c| <= r are solid; 1: nodes with |x - c| >= r are  */
+  int32_t pad;
+} lbm_circle;
+
+/* Solid geometry.  A node is solid if any circle or wall makes it solid.  The wall fraction q of a
+ * link (Eq. 6) is the smallest t in (0, 1] at which x_b + t e_a meets a circle whose solid region
+ * holds x_s = x_b + e_a, or the wall's q when x_s is a wall row.  Every circle, widened by two
+ * nodes, must lie inside the box: links never cross the periodic seam into a circle. */
+typedef struct {
+  int32_t nx, ny;       /* lattice size, each in [4, 65536], nx*ny < 2^31                */
+  int32_t n_circles;    /* number of entries in circles (may be 0)                        */
+  int32_t pad;
+  const lbm_circle* circles;
+  double wall_q_lo;     /* > 0: row 0 is a flat solid wall and its links have this q      */
+  double wall_q_hi;     /* > 0: row ny-1 is a flat solid wall and its links have this q   */
+} lbm_geometry;
+
+/* Fluid model.  psi(rho) of Eq. (16): LBM_EOS_EXP psi0*exp(-rho0/rho) (Sec. 3.2); LBM_EOS_CS
+ * psi = sqrt(2 (p(rho) - rho/3) / G) with the Carnahan-Starling pressure
+ * p = rho R T (1 + eta + eta^2 - eta^3)/(1 - eta)^3 - a rho^2, eta = b rho / 4, T = T_over_Tc*T_c;
+ * LBM_EOS_NONE: single phase (no interaction force).  Solid nodes take psi(rho_wall), the
+ * virtual wall density that sets the contact angle (Sec. 3.2).  Body force density:
+ * rho*(gx, gy) plus azim_C / r along e_theta about (azim_cx, azim_cy) when azim_C != 0. */
+typedef struct {
+  int32_t kind; /* lbm_eos_kind */
+  int32_t pad;
+  double G;     /* interaction strength; attractive (phase separating) when negative        */
+  double psi0, rho0;
+  double a, b, R, T_over_Tc;
+  double rho_wall;
+  double gx, gy;
+  double azim_C, azim_cx, azim_cy;
+} lbm_eos;
+
+/* Device allocation hook: return device memory of at least `bytes` bytes (256-byte aligned) or
+ * NULL.  When no hook is given the library uses cudaMallocAsync/cudaFreeAsync on its stream. */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
+typedef void (*lbm_free_fn)(void* ptr, void* user);
+
+typedef struct {
+  int32_t precision;   /* lbm_precision, default LBM_FP64                                     */
+  int32_t graph_steps; /* time steps per captured CUDA graph in lbm_step; 0 = default (32)    */
+  void* stream;        /* cudaStream_t for all work of the context; NULL = legacy default     */
+  lbm_alloc_fn alloc;  /* optional device allocation hook (both or neither)                   */
+  lbm_free_fn free;
+  void* alloc_user;
+  double rho_ref;      /* reference density of the deviation formats; <= 0: 1.0               */
+} lbm_options;
+
+typedef struct {
+  int32_t nx, ny;
+  int64_t n_fluid;          /* fluid nodes                                                   */
+  int64_t n_boundary_nodes; /* fluid nodes with at least one cut link                        */
+  int64_t n_links;          /* cut links                                                     */
+  int64_t steps;            /* time steps taken since the last initialisation                */
+  int64_t device_bytes;     /* device memory held by the context                             */
+  int64_t fallbacks;        /* reserved: links that fell back to a simpler scheme (r8)        */
+  double T;                 /* absolute temperature of the Carnahan-Starling EOS (0 otherwise) */
+  double psi_wall;          /* psi(rho_wall)                                                 */
+} lbm_info_t;
+
+/* Create a context: validates the arguments, builds on the GPU the solid flags and the list of
+ * boundary links with q (Eq. 6) in canonical order (node index, then direction), and allocates
+ * two population lattices.  tau > 0.5 is the relaxation time (nu = (tau - 1/2)/3).  `opt` may be
+ * NULL.  On success *out receives the context; on failure *out is NULL. */
+lbm_status lbm_create(const lbm_geometry* geometry, const lbm_eos* eos, double tau, int32_t scheme,
+                      const lbm_options* opt, lbm_ctx** out);
+
+/* Maxwell equal-area coexistence densities of the Carnahan-Starling EOS at eos->T_over_Tc
+ * (host computation, no context needed).  LBM_EINVAL unless kind == LBM_EOS_CS and T < T_c. */
+lbm_status lbm_coexistence(const lbm_eos* eos, double* rho_l, double* rho_v);
+
+/* Initialise f = f_eq(rho, u) (Eq. 4) at every fluid node from caller-owned host arrays of nx*ny
+ * doubles (ux, uy may be NULL for zero).  Blocks until the upload is done. */
+lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
+
+/* Initialise a droplet: rho = (rho_in + rho_out)/2 - (rho_in - rho_out)/2 tanh(2 (r - R)/W),
+ * r the distance to (cx, cy), u = 0, f = f_eq (computed on the GPU). */
+lbm_status lbm_init_droplet(lbm_ctx* ctx, double cx, double cy, double R, double W, double rho_in,
+                            double rho_out);
+
+/* Advance n >= 0 time steps, asynchronously on the context's stream (whole graphs of
+ * graph_steps steps, the remainder launched one by one). */
+lbm_status lbm_step(lbm_ctx* ctx, int32_t n);
+
+/* Advance n >= 1 steps without graphs, recording CUDA events around every kernel on the
+ * context's stream; blocks until done and returns the summed milliseconds of the fused step
+ * kernel, of the boundary kernel, and from the first event to the last.  Any pointer may be NULL. */
+lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t n, double* ms_step_kernel, double* ms_boundary,
+                          double* ms_total);
+
+/* Total mass sum over fluid nodes and directions of f (FP64, fixed summation order, so repeated
+ * calls on the same state agree bit for bit).  Blocks.  Returns LBM_EUNSTABLE (sticky) when a
+ * fluid density is not finite or not positive. */
+lbm_status lbm_mass(lbm_ctx* ctx, double* out);
+
+/* Density and velocity (Eq. 5, with the half-force term) of every node into caller-owned host
+ * arrays of nx*ny doubles; solid nodes get NaN.  Blocks. */
+lbm_status lbm_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy);
+
+/* The same into device arrays of nx*ny doubles, asynchronously on the context's stream. */
+lbm_status lbm_fields_device(lbm_ctx* ctx, double* rho, double* ux, double* uy);
+
+/* Node flags into a caller-owned host array of nx*ny bytes: bit 0 solid, bit 1 boundary node
+ * (fluid with at least one cut link).  Blocks. */
+lbm_status lbm_flags(lbm_ctx* ctx, uint8_t* flags);
+
+/* Boundary links in canonical order.  *n_inout holds the capacity of the three arrays on entry
+ * and the number of links on return; arrays may be NULL to query the count only.  LBM_EINVAL if
+ * the capacity is too small (the count is still returned).  Blocks. */
+lbm_status lbm_links(lbm_ctx* ctx, int32_t* node, uint8_t* dir, double* q, int64_t* n_inout);
+
+lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
+
+/* Message of the sticky error, or "" when there is none.  Valid until the next call. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+const char* lbm_status_string(lbm_status s);
+
+/* Release device memory and the context (NULL is ignored).  Synchronises the stream. */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

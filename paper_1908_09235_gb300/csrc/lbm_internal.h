@@ -1,0 +1,88 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lbm_gb300.h"
+
+namespace lbm {
+
+// Node flag bits in device memory.  Bits 0 and 1 are the public ones (lbm_flags).
+enum : uint8_t {
+  FLAG_SOLID = 1,     // solid node
+  FLAG_BOUNDARY = 2,  // fluid node with at least one cut link
+  FLAG_MACRO = 4,     // the step kernel stores rho, u here for the boundary pass (x_b and x_f)
+};
+
+// Everything a kernel needs about the model, passed by value.
+struct DevParams {
+  int nx, ny;
+  int N;            // nx * ny
+  int eos;          // lbm_eos_kind
+  int scheme;       // lbm_scheme
+  int has_body;     // gravity or azimuthal force present
+  double tau, omega, guo_pref;  // omega = 1/tau, guo_pref = 1 - 1/(2 tau)
+  double G, psi0, rho0;
+  double a, b4, RT;             // Carnahan-Starling: a, b/4, R*T
+  double two_over_G;
+  double psi_wall;
+  double gx, gy, azC, azcx, azcy;
+  double rho_ref;               // 0 for FP64 storage
+};
+
+struct GeomCircle {
+  double cx, cy, r;
+  int outside;
+  int pad;
+};
+constexpr int kMaxCircles = 16;
+struct GeomParams {
+  int nx, ny, N, n_circles;
+  double wall_q_lo, wall_q_hi;
+  GeomCircle c[kMaxCircles];
+};
+
+// ---- launchers (implemented in the .cu files) ----
+// geometry.cu
+cudaError_t launch_geom_solid(const GeomParams& g, uint8_t* flags, cudaStream_t s);
+// Counts boundary nodes and links per block; returns the per-block totals scanned in `scan`
+// (int2 per block: boundary nodes, links).  Writes the grand totals into totals[0..1].
+cudaError_t launch_geom_count_scan(const GeomParams& g, const uint8_t* flags, int2* block_tot,
+                                   int nblocks, long long* totals, cudaStream_t s);
+int geom_num_blocks(int N);
+cudaError_t launch_geom_emit(const GeomParams& g, uint8_t* flags, const int2* block_off,
+                             int32_t* bnode, int32_t* boff, uint8_t* ldir, double* lq,
+                             cudaStream_t s);
+
+// step.cu
+cudaError_t launch_step(int precision, const DevParams& p, const void* fa, void* fb,
+                        const uint8_t* flags, double* rho_m, double* ux_m, double* uy_m,
+                        bool fields_only, cudaStream_t s);
+
+// boundary.cu
+cudaError_t launch_boundary(int precision, const DevParams& p, int nb, const int32_t* bnode,
+                            const int32_t* boff, const uint8_t* ldir, const double* lq,
+                            const uint8_t* flags, const void* fa, void* fb, const double* rho_m,
+                            const double* ux_m, const double* uy_m, double* carry,
+                            cudaStream_t s);
+
+// ledger.cu
+int ledger_num_blocks(int N);
+cudaError_t launch_mass(int precision, const DevParams& p, const void* f, const uint8_t* flags,
+                        double* partials, int nblocks, double* result, int* err_flag,
+                        cudaStream_t s);
+cudaError_t launch_init_eq(int precision, const DevParams& p, const uint8_t* flags,
+                           const double* rho, const double* ux, const double* uy, void* f,
+                           cudaStream_t s);
+cudaError_t launch_droplet_rho(const DevParams& p, double cx, double cy, double R, double W,
+                               double rho_in, double rho_out, double* rho, double* ux, double* uy,
+                               cudaStream_t s);
+
+// eos_host.cpp
+bool cs_critical_point(double a, double b, double R, double* Tc, double* rhoc);
+bool cs_maxwell(double a, double b, double R, double T, double* rho_l, double* rho_v);
+double host_psi(const DevParams& p, double rho);
+
+}  // namespace lbm

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every declared entry point; host-side logic that
+needs no GPU (argument validation, the Carnahan-Starling set-up) behaves as documented."""
+import ctypes as C
+import math
+import re
+
+import pytest
+
+import oracle as O
+from paper_1908_09235_gb300 import _build, lbm
+
+HEADER = "include/lbm_gb300.h"
+
+
+def _declared():
+    import os
+    src = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), HEADER)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = _build.build()
+    lib = C.CDLL(path)
+    names = _declared()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(lbm.EXPORTS)
+
+
+def test_coexistence_matches_oracle():
+    for t in (0.7, 0.8, 0.86, 0.9, 0.95):
+        eos = lbm.make_eos(lbm.EOS_CS, G=-1.0, a=0.25, b=4.0, R=1.0, T_over_Tc=t)
+        rl, rv = lbm.lbm_coexistence(eos)
+        Tc, _ = O.cs_critical(0.25, 4.0, 1.0)
+        ol, ov = O.cs_coexistence(0.25, 4.0, 1.0, t * Tc)
+        assert rl == pytest.approx(ol, rel=1e-12)
+        assert rv == pytest.approx(ov, rel=1e-12)
+
+
+def test_coexistence_rejects_supercritical():
+    eos = lbm.make_eos(lbm.EOS_CS, G=-1.0, T_over_Tc=1.05)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_coexistence(eos)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("kw", [
+    dict(tau=0.5),                                        # tau must exceed 1/2
+    dict(tau=float("nan")),
+    dict(scheme=lbm.FH, tau=1.0),                         # chi of Eq. (9) is singular
+    dict(scheme=42),
+    dict(nx=3),
+    dict(circles=[(3.0, 50.0, 10.0)]),                    # crosses the periodic seam
+    dict(circles=[(50.0, 50.0, -1.0)]),
+    dict(eos=lbm.make_eos(lbm.EOS_CS, G=1.0, T_over_Tc=0.86)),  # CS needs G < 0
+    dict(eos=lbm.make_eos(lbm.EOS_EXP, G=0.0)),
+    dict(precision=7),
+])
+def test_create_rejects_invalid_arguments_before_touching_the_gpu(kw):
+    # Validation happens before any CUDA call, so this runs without a GPU.
+    args = dict(nx=100, ny=100, tau=1.0, scheme=lbm.HBB, circles=[(50.0, 35.0, 15.0)],
+                eos=lbm.make_eos(), precision=lbm.FP64)
+    args.update(kw)
+    geo = lbm.make_geometry(args["nx"], 100, args["circles"])
+    opt = lbm.Options()
+    opt.precision = args["precision"]
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_create(geo, args["eos"], args["tau"], args["scheme"], opt)
+    assert e.value.status == 1
+
+
+def test_status_strings():
+    lib = lbm.load_library()
+    for s in range(7):
+        assert lib.lbm_status_string(s).decode()
+    assert not math.isnan(1.0)
