@@ -129,7 +129,7 @@ def make_lattice(w, scheme, precision):
     rl, rv = lbm.lbm_coexistence(eos)
     eos.rho_wall = rv
     lat = lbm.Lattice(w.nx, w.ny, w.tau, scheme, circles=w.circles, eos=eos,
-                      precision=precision, rho_ref=0.5 * (rl + rv))
+                      precision=precision)
     lat.init_droplet(*w.drop, rl, rv)
     return lat, (rl, rv)
 
@@ -210,6 +210,26 @@ def run_e2e(w, steps):
     return info["n_fluid"] * steps / dt / 1e6, 24 * n / steps, 24 * n / steps
 
 
+def run_profile_case(args):
+    """A single lattice of side L (cylinder 0.15 L, droplet 0.2 L) stepped a few times; used
+    as the small case of ncu captures."""
+    import torch
+
+    from paper_1908_09235_gb300 import lbm, workloads
+    L = args.profile_case
+    w = workloads.droplet_on_cylinder(L, 0.15 * L, 0.2 * L)
+    lat, _ = make_lattice(w, lbm.SCHEMES[args.scheme], lbm.PRECISIONS[args.precision])
+    lat.step_timed(args.warmup)
+    ms = lat.step_timed(args.steps)
+    torch.cuda.synchronize()
+    info = lat.info()
+    lat.close()
+    print(json.dumps({"profile_case": w.name, "precision": args.precision, "scheme": args.scheme,
+                      "steps": args.steps, "step_kernel_us": 1e3 * ms[0] / args.steps,
+                      "boundary_kernel_us": 1e3 * ms[1] / args.steps,
+                      "fluid_nodes": info["n_fluid"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,6 +238,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--variant-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="only run a droplet-on-cylinder lattice of this side (for ncu)")
+    ap.add_argument("--precision", default="fp32_dev", choices=["fp64", "fp32_dev"])
+    ap.add_argument("--scheme", default="mod_b")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -225,6 +249,8 @@ def main():
     w = workloads.LARGE
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.profile_case:
+        return run_profile_case(args)
 
     import torch
     world, rank, local = dist_setup()

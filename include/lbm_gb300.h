@@ -78,7 +78,7 @@ typedef struct {
  * holds x_s = x_b + e_a, or the wall's q when x_s is a wall row.  Every circle, widened by two
  * nodes, must lie inside the box: links never cross the periodic seam into a circle. */
 typedef struct {
-  int32_t nx, ny;       /* lattice size, each in [4, 65536], nx*ny < 2^31                */
+  int32_t nx, ny;       /* lattice size, each in [4, 65536], 9*nx*ny < 2^31            */
   int32_t n_circles;    /* number of entries in circles (may be 0)                        */
   int32_t pad;
   const lbm_circle* circles;
@@ -115,7 +115,8 @@ typedef struct {
   lbm_alloc_fn alloc;  /* optional device allocation hook (both or neither)                   */
   lbm_free_fn free;
   void* alloc_user;
-  double rho_ref;      /* reference density of the deviation formats; <= 0: 1.0               */
+  double rho_ref;      /* reference density of the deviation formats; <= 0: the smallest       *
+                        * initial fluid density, set by lbm_init_fields / lbm_init_droplet      */
 } lbm_options;
 
 typedef struct {
@@ -125,7 +126,7 @@ typedef struct {
   int64_t n_links;          /* cut links                                                     */
   int64_t steps;            /* time steps taken since the last initialisation                */
   int64_t device_bytes;     /* device memory held by the context                             */
-  int64_t fallbacks;        /* reserved: links that fell back to a simpler scheme (r8)        */
+  int64_t fallbacks;        /* reserved (always 0)                                           */
   double T;                 /* absolute temperature of the Carnahan-Starling EOS (0 otherwise) */
   double psi_wall;          /* psi(rho_wall)                                                 */
 } lbm_info_t;

@@ -3,8 +3,8 @@
 // f_abar(x_b, t+1) from the time-t values, then the per-node leakage of Eq. (15) and the
 // correction of scheme A (Eq. 18) or the fictitious density of scheme B (Eq. 22) / Bao (Eq. 23).
 //
-// One thread per boundary node; its links are consecutive in the CSR arrays.  Arithmetic is FP64
-// for every storage format.  With the push layout of the step kernel (destination lattice B,
+// An 8-lane group per boundary node, one lane per link (the links of a node are consecutive in
+// the CSR arrays).  Arithmetic is FP64 for every storage format.  With the push layout of the step kernel (destination lattice B,
 // source lattice A) the time-t values of a link are found at:
 //   f*_a(x_b)    = B_a(x_s)        (pushed into the solid slot)
 //   f*_abar(x_b) = B_abar(x_f)     f*_a(x_f) = B_a(x_b)      f*_a(x_ff) = B_a(x_f)
@@ -77,6 +77,16 @@ __device__ __forceinline__ bool ghost(const DevParams& p, bool fh, int n, int nf
   return true;
 }
 
+// Sum over the 8 lanes of a node's group in a fixed tree order (bitwise reproducible).
+__device__ __forceinline__ double group8_sum(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// One 8-lane group per boundary node, one lane per cut link (a fluid node has at most 8), so the
+// loads of all links of a node are in flight together; per-node sums use group8_sum.
 template <typename S>
 __global__ void __launch_bounds__(128) boundary_kernel(DevParams p, int nb,
                                                        const int32_t* __restrict__ bnode,
@@ -88,53 +98,61 @@ __global__ void __launch_bounds__(128) boundary_kernel(DevParams p, int nb,
                                                        const double* __restrict__ ux_m,
                                                        const double* __restrict__ uy_m,
                                                        double* __restrict__ carry) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = gt >> 3, k = gt & 7;
+  const bool node_ok = b < nb;
   const int nx = p.nx, ny = p.ny, scheme = p.scheme;
-  const int n = bnode[b];
-  const int i = n % nx, j = n / nx;
-  const int l0 = boff[b], l1 = boff[b + 1];
-  const double rho_b = rho_m[n], ubx = ux_m[n], uby = uy_m[n];
+  int n = 0, l0 = 0, nl = 0;
+  if (node_ok) {
+    n = bnode[b];
+    l0 = boff[b];
+    nl = boff[b + 1] - l0;
+  }
+  const bool act = node_ok && k < nl;
   const bool ghost_family = scheme == LBM_FH || scheme == LBM_MLS || scheme == LBM_MOD_A ||
                             scheme == LBM_MOD_B || scheme == LBM_BAO;
   const bool fh = scheme == LBM_FH;
 
+  int a = 1, ab = 3, nf = 0, ns = 0, nff = 0;
+  double q = 0.5, fo = 0.0, rho_b = 1.0, ubx = 0.0, uby = 0.0;
+  bool f_solid = false, ff_solid = false;
+  if (act) {
+    const int i = n % nx, j = n / nx;
+    a = ldir[l0 + k];
+    ab = opposite(a);
+    q = lq[l0 + k];
+    ns = wrap_once(j + ey(a), ny) * nx + wrap_once(i + ex(a), nx);
+    nf = wrap_once(j - ey(a), ny) * nx + wrap_once(i - ex(a), nx);
+    nff = wrap_once(j - 2 * ey(a), ny) * nx + wrap_once(i - 2 * ex(a), nx);
+    f_solid = flags[nf] & FLAG_SOLID;
+    ff_solid = flags[nff] & FLAG_SOLID;
+    fo = L.B(a, ns);  // outgoing f*_a(x_b, t)
+    rho_b = rho_m[n];
+    ubx = ux_m[n];
+    uby = uy_m[n];
+  }
+  double chi = 0.0, usx = 0.0, usy = 0.0;
+  bool gh = false;
+  if (act && ghost_family)
+    gh = ghost(p, fh, n, nf, f_solid, q, ux_m, uy_m, &chi, &usx, &usy);
+
   double rho_s = rho_b;
   if (scheme == LBM_MOD_B || scheme == LBM_BAO) {
     double num = 0.0, den = 0.0;
-    for (int l = l0; l < l1; ++l) {
-      const int a = ldir[l];
-      const int nf = wrap_once(j - ey(a), ny) * nx + wrap_once(i - ex(a), nx);
-      const int ns = wrap_once(j + ey(a), ny) * nx + wrap_once(i + ex(a), nx);
-      double chi, usx, usy;
-      if (!ghost(p, false, n, nf, flags[nf] & FLAG_SOLID, lq[l], ux_m, uy_m, &chi, &usx, &usy))
-        continue;  // halfway bounce-back on this link: chi = 0
+    if (gh) {  // links without a ghost value (MLS fallback) are halfway bounce-back: chi = 0
       const double br = bracket(a, usx, usy, ubx, uby);
-      const double fo = L.B(a, ns);
-      if (scheme == LBM_MOD_B) {
-        num += chi * fo;  // Eq. (22)
-        den += chi * br;
-      } else {
-        num += fo;  // Eq. (23)
-        den += br;
-      }
+      num = scheme == LBM_MOD_B ? chi * fo : fo;  // Eq. (22) / Eq. (23)
+      den = scheme == LBM_MOD_B ? chi * br : br;
     }
+    num = group8_sum(num);
+    den = group8_sum(den);
     if (den != 0.0) rho_s = num / den;
   }
 
-  double sum_out = 0.0, sum_in = 0.0, resid = 0.0;
-  for (int l = l0; l < l1; ++l) {
-    const int a = ldir[l], ab = opposite(a);
-    const double q = lq[l];
-    const int ns = wrap_once(j + ey(a), ny) * nx + wrap_once(i + ex(a), nx);
-    const int nf = wrap_once(j - ey(a), ny) * nx + wrap_once(i - ex(a), nx);
-    const int nff = wrap_once(j - 2 * ey(a), ny) * nx + wrap_once(i - 2 * ex(a), nx);
-    const bool f_solid = flags[nf] & FLAG_SOLID;
-    const double fo = L.B(a, ns);  // outgoing f*_a(x_b, t)
-    double val = fo;
+  double val = fo;
+  if (act) {
     if (ghost_family) {
-      double chi, usx, usy;
-      if (ghost(p, fh, n, nf, f_solid, q, ux_m, uy_m, &chi, &usx, &usy)) {
+      if (gh) {
         const double rr = (scheme == LBM_MOD_B || scheme == LBM_BAO) ? rho_s : rho_b;
         const double feq_s = rr * bracket(a, usx, usy, ubx, uby);  // Eq. (8) / Eq. (20)
         val = (1.0 - chi) * fo + chi * feq_s;                      // Eq. (7) / Eq. (17)
@@ -146,7 +164,6 @@ __global__ void __launch_bounds__(128) boundary_kernel(DevParams p, int nb,
         val = 1.0 / (2.0 * q) * fo + (2.0 * q - 1.0) / (2.0 * q) * L.B(ab, nf);
       }
     } else if (scheme == LBM_BOUZIDI_Q) {  // Eq. (13)
-      const bool ff_solid = flags[nff] & FLAG_SOLID;
       if (q < 0.5) {
         if (!f_solid) {
           if (ff_solid)
@@ -165,21 +182,25 @@ __global__ void __launch_bounds__(128) boundary_kernel(DevParams p, int nb,
     } else if (scheme == LBM_ZHAO_YONG) {  // Eq. (14)
       val = 2.0 * q / (1.0 + 2.0 * q) * L.B(ab, nf) + 1.0 / (1.0 + 2.0 * q) * L.A(a, n);
     }
-    resid += L.storeB(ab, n, val);
-    sum_out += fo;
-    sum_in += val;
   }
-  const bool conserving = scheme == LBM_MOD_A || scheme == LBM_MOD_B ||
-                          scheme == LBM_BOUZIDI_L_A || scheme == LBM_HBB;
-  if (scheme == LBM_MOD_A || scheme == LBM_BOUZIDI_L_A) {
-    const double dm = sum_out - sum_in;  // Eq. (15)
-    double f0 = L.B(0, n) + dm;          // Eq. (18)
-    if (L.dev) f0 += carry[b];
-    resid += L.storeB(0, n, f0);
-  } else if (L.dev && conserving && carry[b] != 0.0) {
-    resid += L.storeB(0, n, L.B(0, n) + carry[b]);
+  double resid = 0.0;
+  if (act) resid = L.storeB(ab, n, val);
+
+  const bool fix_f0 = scheme == LBM_MOD_A || scheme == LBM_BOUZIDI_L_A;
+  const bool conserving = fix_f0 || scheme == LBM_MOD_B || scheme == LBM_HBB;
+  double dm = 0.0;
+  if (fix_f0) dm = group8_sum(act ? fo - val : 0.0);  // Eq. (15)
+  if (L.dev && conserving) resid = group8_sum(resid);
+  if (node_ok && k == 0) {
+    if (fix_f0) {
+      double f0 = L.B(0, n) + dm;  // Eq. (18)
+      if (L.dev) f0 += carry[b];
+      resid += L.storeB(0, n, f0);
+    } else if (L.dev && conserving && carry[b] != 0.0) {
+      resid += L.storeB(0, n, L.B(0, n) + carry[b]);
+    }
+    if (L.dev && conserving) carry[b] = resid;
   }
-  if (L.dev && conserving) carry[b] = resid;
 }
 
 template <typename S>
@@ -188,8 +209,9 @@ cudaError_t launch_b(const DevParams& p, int nb, const int32_t* bnode, const int
                      void* fb, const double* rho_m, const double* ux_m, const double* uy_m,
                      double* carry, cudaStream_t s) {
   Lat<S> L{(const S*)fa, (S*)fb, (size_t)p.N, p.rho_ref};
-  boundary_kernel<S><<<(nb + 127) / 128, 128, 0, s>>>(p, nb, bnode, boff, ldir, lq, flags, L,
-                                                        rho_m, ux_m, uy_m, carry);
+  const long long threads = 8LL * nb;
+  boundary_kernel<S><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
+      p, nb, bnode, boff, ldir, lq, flags, L, rho_m, ux_m, uy_m, carry);
   return cudaGetLastError();
 }
 

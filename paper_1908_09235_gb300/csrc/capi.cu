@@ -51,6 +51,7 @@ struct lbm_ctx {
   lbm_status status = LBM_OK;
   std::string msg;
   double T = 0.0;
+  bool rho_ref_auto = false;  // deviation storage: take rho_ref from the initial state
 };
 
 namespace {
@@ -185,7 +186,7 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
   *out = nullptr;
   if (!geo || !eos) return LBM_EINVAL;
   if (geo->nx < 4 || geo->ny < 4 || geo->nx > 65536 || geo->ny > 65536) return LBM_EINVAL;
-  if ((long long)geo->nx * geo->ny >= (1LL << 31)) return LBM_EINVAL;
+  if (9LL * geo->nx * geo->ny >= (1LL << 31)) return LBM_EINVAL;  // 32-bit element offsets
   if (geo->n_circles < 0 || geo->n_circles > kMaxCircles) return LBM_EINVAL;
   if (geo->n_circles > 0 && !geo->circles) return LBM_EINVAL;
   if (!(tau > 0.5) || !is_fin(tau)) return LBM_EINVAL;
@@ -235,6 +236,7 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
   p.azcy = eos->azim_cy;
   p.has_body = (eos->gx != 0.0 || eos->gy != 0.0 || eos->azim_C != 0.0) ? 1 : 0;
   p.rho_ref = precision == LBM_FP64 ? 0.0 : ((opt && opt->rho_ref > 0) ? opt->rho_ref : 1.0);
+  c->rho_ref_auto = precision != LBM_FP64 && !(opt && opt->rho_ref > 0);
   if (eos->kind == LBM_EOS_CS) {
     double Tc, rhoc;
     if (!(eos->G < 0) || !cs_critical_point(eos->a, eos->b, eos->R, &Tc, &rhoc) ||
@@ -257,6 +259,7 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
   }
   p.two_over_G = eos->kind != LBM_EOS_NONE ? 2.0 / eos->G : 0.0;
   p.psi_wall = eos->kind != LBM_EOS_NONE ? host_psi(p, eos->rho_wall) : 0.0;
+  finalize_consts(p);
 
   GeomParams& g = c->g;
   g.nx = geo->nx;
@@ -376,6 +379,11 @@ void lbm_destroy(lbm_ctx* c) {
 
 static lbm_status init_common(lbm_ctx* c) {
   const size_t N = (size_t)c->p.N;
+  for (int k = 0; k < 2; ++k)  // kernel parameters (rho_ref) may have changed
+    if (c->graph[k]) {
+      cudaGraphExecDestroy(c->graph[k]);
+      c->graph[k] = nullptr;
+    }
   LBM_CUDA(c, launch_init_eq(c->precision, c->p, c->flags, c->rho_m, c->ux_m, c->uy_m, c->f[0],
                              c->stream));
   LBM_CUDA(c, cudaMemsetAsync(c->f[1], 0, 9 * N * c->pop_bytes, c->stream));
@@ -392,6 +400,13 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, cons
   if (c->status) return c->status;
   if (!rho) return LBM_EINVAL;
   const size_t N = (size_t)c->p.N;
+  if (c->rho_ref_auto) {  // smallest positive finite initial density
+    double m = 0.0;
+    for (size_t k = 0; k < N; ++k)
+      if (std::isfinite(rho[k]) && rho[k] > 0 && (m == 0.0 || rho[k] < m)) m = rho[k];
+    if (m > 0) c->p.rho_ref = m;
+    finalize_consts(c->p);
+  }
   LBM_CUDA(c, cudaMemcpyAsync(c->rho_m, rho, N * 8, cudaMemcpyHostToDevice, c->stream));
   if (ux)
     LBM_CUDA(c, cudaMemcpyAsync(c->ux_m, ux, N * 8, cudaMemcpyHostToDevice, c->stream));
@@ -410,6 +425,10 @@ lbm_status lbm_init_droplet(lbm_ctx* c, double cx, double cy, double R, double W
   if (c->status) return c->status;
   if (!(W > 0) || !(rho_in > 0) || !(rho_out > 0) || !is_fin(cx) || !is_fin(cy) || !is_fin(R))
     return LBM_EINVAL;
+  if (c->rho_ref_auto) {
+    c->p.rho_ref = rho_in < rho_out ? rho_in : rho_out;
+    finalize_consts(c->p);
+  }
   LBM_CUDA(c, launch_droplet_rho(c->p, cx, cy, R, W, rho_in, rho_out, c->rho_m, c->ux_m, c->uy_m,
                                  c->stream));
   return init_common(c);

@@ -37,15 +37,15 @@ __device__ __forceinline__ int wrap_any(int v, int n) {
 // psi(rho): exponential psi0 exp(-rho0/rho) (Sec. 3.2) or the Carnahan-Starling form
 // sqrt(2 (p - rho/3)/G); zero for a single-phase fluid.
 template <typename C, int EOS>
-__device__ __forceinline__ C psi_of(const DevParams& p, C rho) {
+__device__ __forceinline__ C psi_of(const Consts<C>& k, C rho) {
   if constexpr (EOS == LBM_EOS_EXP) {
-    return C(p.psi0) * exp(-C(p.rho0) / rho);
+    return k.psi0 * exp(-k.rho0 / rho);
   } else if constexpr (EOS == LBM_EOS_CS) {
-    C eta = C(p.b4) * rho;
-    C om = C(1) - eta;
-    C num = C(1) + eta + eta * eta - eta * eta * eta;
-    C pr = rho * C(p.RT) * num / (om * om * om) - C(p.a) * rho * rho;
-    return sqrt((pr - rho / C(3)) * C(p.two_over_G));
+    const C eta = k.b4 * rho;
+    const C om = C(1) - eta;
+    const C num = C(1) + eta + eta * eta - eta * eta * eta;
+    const C pr = rho * k.RT * num / (om * om * om) - k.a * rho * rho;
+    return sqrt((pr - rho * C(1.0 / 3.0)) * k.two_over_G);
   } else {
     return C(0);
   }

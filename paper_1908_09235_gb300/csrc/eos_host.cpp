@@ -126,6 +126,32 @@ bool cs_maxwell(double a, double b, double R, double T, double* rho_l, double* r
   return std::isfinite(rl) && std::isfinite(rv) && rv < rl;
 }
 
+template <typename C>
+static void fill(Consts<C>& k, const DevParams& p) {
+  k.omega = C(p.omega);
+  k.one_m_omega = C(1.0 - p.omega);
+  k.K = C(3.0 * p.guo_pref);
+  k.G = C(p.G);
+  k.psi0 = C(p.psi0);
+  k.rho0 = C(p.rho0);
+  k.a = C(p.a);
+  k.b4 = C(p.b4);
+  k.RT = C(p.RT);
+  k.two_over_G = C(p.two_over_G);
+  k.psi_wall = C(p.psi_wall);
+  k.gx = C(p.gx);
+  k.gy = C(p.gy);
+  k.azC = C(p.azC);
+  k.azcx = C(p.azcx);
+  k.azcy = C(p.azcy);
+  k.rho_ref = C(p.rho_ref);
+}
+
+void finalize_consts(DevParams& p) {
+  fill(p.cd, p);
+  fill(p.cf, p);
+}
+
 double host_psi(const DevParams& p, double rho) {
   if (p.eos == LBM_EOS_EXP) return p.psi0 * std::exp(-p.rho0 / rho);
   if (p.eos == LBM_EOS_CS) {

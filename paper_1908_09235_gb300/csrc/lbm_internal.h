@@ -16,6 +16,16 @@ enum : uint8_t {
   FLAG_MACRO = 4,     // the step kernel stores rho, u here for the boundary pass (x_b and x_f)
 };
 
+// Model constants in the arithmetic type of a kernel (precomputed on the host so that FP32
+// kernels convert nothing from FP64 at run time).
+template <typename C>
+struct Consts {
+  C omega, one_m_omega, K;     // 1/tau, 1 - 1/tau, 3 (1 - 1/(2 tau))
+  C G, psi0, rho0, a, b4, RT, two_over_G, psi_wall;
+  C gx, gy, azC, azcx, azcy;
+  C rho_ref;
+};
+
 // Everything a kernel needs about the model, passed by value.
 struct DevParams {
   int nx, ny;
@@ -30,7 +40,16 @@ struct DevParams {
   double psi_wall;
   double gx, gy, azC, azcx, azcy;
   double rho_ref;               // 0 for FP64 storage
+  Consts<double> cd;
+  Consts<float> cf;
+  template <typename C>
+  __host__ __device__ const Consts<C>& k() const {
+    if constexpr (sizeof(C) == 8) return cd; else return cf;
+  }
 };
+
+// Fill cd and cf from the double fields above (host, after any change of those fields).
+void finalize_consts(DevParams& p);
 
 struct GeomCircle {
   double cx, cy, r;

@@ -7,17 +7,18 @@
 // including into solid nodes, whose slots then hold the outgoing populations the boundary pass
 // reads.  Every population is read once and written once per step.
 //
-// A CTA covers a TX x TY tile.  Each thread keeps its node's 9 populations in registers; psi of
-// the tile and of a one-node ring around it goes to shared memory (ring nodes recompute their
-// density from their own 9 populations), so the force needs no second pass over memory.
+// A CTA covers a 32 x (8 RY) tile; each thread keeps the 9 populations of its RY nodes in
+// registers.  psi of the tile and of a one-node ring around it goes to shared memory (ring nodes
+// recompute their density from their own 9 populations), so the force needs no second pass over
+// memory.  RY = 4 rows per thread for FP32 storage, 2 for FP64 (register budget).
 #include "d2q9.cuh"
 
 namespace lbm {
 
 namespace {
 
-constexpr int TX = 32;
-constexpr int TY = 8;
+constexpr int TX = 32;   // threads (and nodes) of a tile in x
+constexpr int TYT = 8;   // threads of a tile in y; each handles RY rows, TYT apart
 
 template <typename S>
 struct StoreTraits;
@@ -25,183 +26,229 @@ template <>
 struct StoreTraits<double> {
   using C = double;  // compute type
   static constexpr bool deviation = false;
+  static constexpr int RY = 2;  // rows per thread (register budget of FP64)
 };
 template <>
 struct StoreTraits<float> {
   using C = float;
   static constexpr bool deviation = true;  // stores f_a - w_a rho_ref
+  static constexpr int RY = 4;
 };
 
-// Density of the node at linear index m from its nine stored values (deviation-aware).
-template <typename S>
-__device__ __forceinline__ typename StoreTraits<S>::C node_rho(const S* __restrict__ f, size_t N,
-                                                              int m, typename StoreTraits<S>::C rho_ref) {
-  using C = typename StoreTraits<S>::C;
-  C r = C(f[m]);
+// Sum of the nine stored values in direction order (a node's density, less rho_ref for the
+// deviation format).  Own nodes and ring nodes use the same arithmetic, so every CTA that needs
+// psi of a node computes the same value.
+template <typename C>
+__device__ __forceinline__ C pop_sum(const C (&f)[9]) {
+  C r = f[0];
 #pragma unroll
-  for (int a = 1; a < 9; ++a) r += C(f[a * N + m]);
-  if constexpr (StoreTraits<S>::deviation) r += rho_ref;
+  for (int a = 1; a < 9; ++a) r += f[a];
   return r;
 }
 
 template <typename S, int EOS, bool FIELDS>
-__global__ void __launch_bounds__(TX* TY) step_kernel(DevParams p, const S* __restrict__ fa,
-                                                      S* __restrict__ fb,
-                                                      const uint8_t* __restrict__ flags,
-                                                      double* __restrict__ rho_m,
-                                                      double* __restrict__ ux_m,
-                                                      double* __restrict__ uy_m) {
+__global__ void __launch_bounds__(TX* TYT, sizeof(S) == 4 ? 4 : 2) step_kernel(DevParams p, const S* __restrict__ fa,
+                                                       S* __restrict__ fb,
+                                                       const uint8_t* __restrict__ flags,
+                                                       double* __restrict__ rho_m,
+                                                       double* __restrict__ ux_m,
+                                                       double* __restrict__ uy_m) {
   using C = typename StoreTraits<S>::C;
   constexpr bool DEV = StoreTraits<S>::deviation;
-  __shared__ C psi_s[TY + 2][TX + 2];
+  constexpr int RY = StoreTraits<S>::RY;
+  constexpr int TH = TYT * RY;  // tile height in nodes
+  __shared__ C psi_s[TH + 2][TX + 2];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int x = x0 + tx, y = y0 + ty;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TH;
   const int nx = p.nx, ny = p.ny;
-  const size_t N = (size_t)p.N;
-  const bool inside = (x < nx) && (y < ny);
-  const C rho_ref = DEV ? C(p.rho_ref) : C(0);
-  const C psi_w = C(p.psi_wall);
+  const int N = p.N;  // 9 N < 2^31 (checked at creation): 32-bit element offsets
+  // ragged tiles of lattices narrower than a tile wrap more than once
+  const bool small = nx <= TX + 1 || ny <= TH + 1;
+  const Consts<C>& k = p.k<C>();
+  const C rho_ref = DEV ? k.rho_ref : C(0);
+  const C psi_w = k.psi_wall;
 
-  // Own node (out-of-range threads of a ragged tile stand in for the wrapped node).
-  const int xo = inside ? x : wrap_any(x, nx);
-  const int yo = inside ? y : wrap_any(y, ny);
-  const int n = yo * nx + xo;
-  const uint8_t fl = flags[n];
-  const bool solid = fl & FLAG_SOLID;
-  C f[9];
-  C rho = C(1);
-  if (!solid) {
+  // ---- phase 1: own nodes' populations, density and psi; psi of the ring ----
+  const int x = x0 + tx;
+  const int xo = x < nx ? x : (small ? wrap_any(x, nx) : x - nx);
+  C f[RY][9];
+  C rho[RY];
+  uint8_t fl[RY];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) f[a] = C(fa[a * N + n]);
-    rho = f[0];
+  for (int r = 0; r < RY; ++r) {
+    const int y = y0 + ty + r * TYT;
+    const int yo = y < ny ? y : (small ? wrap_any(y, ny) : y - ny);
+    const int n = yo * nx + xo;
+    fl[r] = flags[n];
+    rho[r] = C(1);
+    if (!(fl[r] & FLAG_SOLID)) {
 #pragma unroll
-    for (int a = 1; a < 9; ++a) rho += f[a];
-    if constexpr (DEV) rho += rho_ref;
+      for (int a = 0; a < 9; ++a) f[r][a] = C(fa[a * N + n]);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) f[r][a] = C(0);
+    }
   }
   if constexpr (EOS != LBM_EOS_NONE) {
-    psi_s[ty + 1][tx + 1] = solid ? psi_w : psi_of<C, EOS>(p, rho);
-    // one-node ring around the tile: 2 (TX + 2) + 2 TY cells
-    const int tid = ty * TX + tx;
-    constexpr int kRing = 2 * (TX + 2) + 2 * TY;
-    for (int k = tid; k < kRing; k += TX * TY) {
-      int hx, hy;
-      if (k < TX + 2) {
-        hx = k;
-        hy = 0;
-      } else if (k < 2 * (TX + 2)) {
-        hx = k - (TX + 2);
-        hy = TY + 1;
-      } else if (k < 2 * (TX + 2) + TY) {
-        hx = 0;
-        hy = k - 2 * (TX + 2) + 1;
+    // One-node ring around the tile, 2 (TX + 2) + 2 TH cells, one per thread of the first
+    // kRing threads.  Its loads are issued before any own node's psi is computed, so a CTA
+    // waits for memory once.
+    constexpr int kRing = 2 * (TX + 2) + 2 * TH;
+    static_assert(kRing <= TX * TYT, "one ring cell per thread");
+    const int c = ty * TX + tx;
+    int hx = 0, hy = 0;
+    bool ring_fluid = false;
+    C v[9];
+    if (c < kRing) {
+      if (c < 2 * (TX + 2)) {
+        hx = c < TX + 2 ? c : c - (TX + 2);
+        hy = c < TX + 2 ? 0 : TH + 1;
       } else {
-        hx = TX + 1;
-        hy = k - 2 * (TX + 2) - TY + 1;
+        const int kk = c - 2 * (TX + 2);
+        hx = kk < TH ? 0 : TX + 1;
+        hy = (kk < TH ? kk : kk - TH) + 1;
       }
-      const int gxh = wrap_any(x0 - 1 + hx, nx), gyh = wrap_any(y0 - 1 + hy, ny);
-      const int m = gyh * nx + gxh;
-      C ps;
-      if (flags[m] & FLAG_SOLID)
-        ps = psi_w;
-      else
-        ps = psi_of<C, EOS>(p, node_rho<S>(fa, N, m, rho_ref));
-      psi_s[hy][hx] = ps;
+      int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+      if (small) {
+        gx = wrap_any(gx, nx);
+        gy = wrap_any(gy, ny);
+      } else {
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+      }
+      const int m = gy * nx + gx;
+      ring_fluid = !(flags[m] & FLAG_SOLID);
+      if (ring_fluid) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = C(fa[a * N + m]);
+      }
     }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      if (!(fl[r] & FLAG_SOLID)) rho[r] = rho_ref + pop_sum<C>(f[r]);
+      psi_s[ty + r * TYT + 1][tx + 1] = (fl[r] & FLAG_SOLID) ? psi_w : psi_of<C, EOS>(k, rho[r]);
+    }
+    if (c < kRing) psi_s[hy][hx] = ring_fluid ? psi_of<C, EOS>(k, rho_ref + pop_sum<C>(v)) : psi_w;
     __syncthreads();
-  }
-  if (!inside) return;
-  if (solid) {
-    if constexpr (FIELDS) {
-      const double nan = __longlong_as_double(0x7ff8000000000000LL);
-      rho_m[n] = nan;
-      ux_m[n] = nan;
-      uy_m[n] = nan;
-    }
-    return;
-  }
-
-  // Total force: Eq. (16) plus body forces.
-  C Fx = C(0), Fy = C(0);
-  if constexpr (EOS != LBM_EOS_NONE) {
-    const int cx = tx + 1, cy = ty + 1;
-    // sum_a w_a psi(x + e_a) e_a, accumulated in direction order 1..8
-    C sx = wpsi<C>(1) * psi_s[cy][cx + 1];
-    sx -= wpsi<C>(3) * psi_s[cy][cx - 1];
-    sx += wpsi<C>(5) * psi_s[cy + 1][cx + 1];
-    sx -= wpsi<C>(6) * psi_s[cy + 1][cx - 1];
-    sx -= wpsi<C>(7) * psi_s[cy - 1][cx - 1];
-    sx += wpsi<C>(8) * psi_s[cy - 1][cx + 1];
-    C sy = wpsi<C>(2) * psi_s[cy + 1][cx];
-    sy -= wpsi<C>(4) * psi_s[cy - 1][cx];
-    sy += wpsi<C>(5) * psi_s[cy + 1][cx + 1];
-    sy += wpsi<C>(6) * psi_s[cy + 1][cx - 1];
-    sy -= wpsi<C>(7) * psi_s[cy - 1][cx - 1];
-    sy -= wpsi<C>(8) * psi_s[cy - 1][cx + 1];
-    const C mg = -C(p.G) * psi_s[cy][cx];
-    Fx = mg * sx;
-    Fy = mg * sy;
-  }
-  if (p.has_body) {
-    Fx += rho * C(p.gx);
-    Fy += rho * C(p.gy);
-    if (p.azC != 0.0) {
-      C dx = C(x) - C(p.azcx), dy = C(y) - C(p.azcy);
-      C r2 = dx * dx + dy * dy;
-      Fx += C(p.azC) * (-dy) / r2;
-      Fy += C(p.azC) * dx / r2;
-    }
-  }
-
-  // Velocity with the half-force term, Eq. (5).
-  C mx = f[1];
-  mx -= f[3];
-  mx += f[5];
-  mx -= f[6];
-  mx -= f[7];
-  mx += f[8];
-  C my = f[2];
-  my -= f[4];
-  my += f[5];
-  my += f[6];
-  my -= f[7];
-  my -= f[8];
-  const C ux = (mx + C(0.5) * Fx) / rho;
-  const C uy = (my + C(0.5) * Fy) / rho;
-
-  if constexpr (FIELDS) {
-    rho_m[n] = double(rho);
-    ux_m[n] = double(ux);
-    uy_m[n] = double(uy);
-    return;
   } else {
-    if (fl & FLAG_MACRO) {
-      rho_m[n] = double(rho);
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+      if (!(fl[r] & FLAG_SOLID)) rho[r] = rho_ref + pop_sum<C>(f[r]);
+  }
+
+  // ---- phase 2: force, velocity, collision and push of each own node ----
+  const C omega = k.omega, one_m_omega = k.one_m_omega;
+  const C K = k.K;  // 3 (1 - 1/(2 tau)): Guo prefactor times 1/c_s^2
+  const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    const int y = y0 + ty + r * TYT;
+    if (x >= nx || y >= ny) continue;
+    const int n = y * nx + x;
+    if (fl[r] & FLAG_SOLID) {
+      if constexpr (FIELDS) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        rho_m[n] = nan;
+        ux_m[n] = nan;
+        uy_m[n] = nan;
+      }
+      continue;
+    }
+    const C rh = rho[r];
+    // Total force: Eq. (16) plus body forces.
+    C Fx = C(0), Fy = C(0);
+    if constexpr (EOS != LBM_EOS_NONE) {
+      const int cx = tx + 1, cy = ty + r * TYT + 1;
+      // sum_a w_a psi(x + e_a) e_a as weighted differences of opposite neighbours: the
+      // subtractions of nearly equal psi are exact, which keeps FP32 forces accurate in smooth
+      // regions
+      const C d13 = psi_s[cy][cx + 1] - psi_s[cy][cx - 1];
+      const C d24 = psi_s[cy + 1][cx] - psi_s[cy - 1][cx];
+      const C d57 = psi_s[cy + 1][cx + 1] - psi_s[cy - 1][cx - 1];
+      const C d86 = psi_s[cy - 1][cx + 1] - psi_s[cy + 1][cx - 1];
+      const C sx = wpsi<C>(1) * d13 + wpsi<C>(5) * (d57 + d86);
+      const C sy = wpsi<C>(2) * d24 + wpsi<C>(5) * (d57 - d86);
+      const C mg = -k.G * psi_s[cy][cx];
+      Fx = mg * sx;
+      Fy = mg * sy;
+    }
+    if (p.has_body) {
+      Fx += rh * k.gx;
+      Fy += rh * k.gy;
+      if (k.azC != C(0)) {
+        const C dx = C(x) - k.azcx, dy = C(y) - k.azcy;
+        const C r2 = dx * dx + dy * dy;
+        Fx += k.azC * (-dy) / r2;
+        Fy += k.azC * dx / r2;
+      }
+    }
+    const C(&g)[9] = f[r];
+    // Velocity with the half-force term, Eq. (5).
+    const C mx = ((g[1] - g[3]) + (g[5] - g[7])) + (g[8] - g[6]);
+    const C my = ((g[2] - g[4]) + (g[5] - g[7])) + (g[6] - g[8]);
+    const C inv_rho = C(1) / rh;
+    const C ux = (mx + C(0.5) * Fx) * inv_rho;
+    const C uy = (my + C(0.5) * Fy) * inv_rho;
+    if constexpr (FIELDS) {
+      rho_m[n] = double(rh);
       ux_m[n] = double(ux);
       uy_m[n] = double(uy);
-    }
-    // Collision, Eq. (2), with f_eq of Eq. (4) and the Guo forcing term, then push (Eq. 3).
-    const C omega = C(p.omega), pref = C(p.guo_pref);
-    const C uu = ux * ux + uy * uy;
-    const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
-    const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+      continue;
+    } else {
+      if (fl[r] & FLAG_MACRO) {
+        rho_m[n] = double(rh);
+        ux_m[n] = double(ux);
+        uy_m[n] = double(uy);
+      }
+      // Collision, Eq. (2): f* = (1 - omega) f + omega f_eq + F_a, with f_eq of Eq. (4),
+      //   f_eq = w [c0 + rho eu (3 + 4.5 eu)],  c0 = rho (1 - 1.5 u.u) (less rho_ref if stored
+      //   as a deviation), and Guo's term F_a = w [K eF (1 + 3 eu) - K u.F], K = 3 (1 - 1/2tau),
+      //   eu = e_a.u, eF = e_a.F.
+      const C uu = ux * ux + uy * uy;
+      const C c0 = (rh - rho_ref) - C(1.5) * rh * uu;
+      const C uF = ux * Fx + uy * Fy;
+      const C A0 = omega * c0 - K * uF;
+      const C orho = omega * rh;
+      // Opposite directions a, abar share |e.u| and |e.F|: h_a = P + Q, h_abar = P - Q with the
+      // even part P = A0 + 4.5 rho omega eu^2 + 3 K eF eu and the odd part
+      // Q = 3 rho omega eu + K eF.
+      C out[9];
+      out[0] = one_m_omega * g[0] + wgt<C>(0) * A0;
+      const C o45 = C(4.5) * orho, o3 = C(3) * orho, K3 = C(3) * K;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      const C eu = C(ex(a)) * ux + C(ey(a)) * uy;
-      const C w = wgt<C>(a);
-      C feq;
-      if constexpr (DEV)
-        feq = w * (rho - rho_ref) + w * rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu);
-      else
-        feq = w * rho * (C(1) + C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu);
-      const C gxa = C(3) * (C(ex(a)) - ux) + C(9) * eu * C(ex(a));
-      const C gya = C(3) * (C(ey(a)) - uy) + C(9) * eu * C(ey(a));
-      const C Fa = pref * w * (gxa * Fx + gya * Fy);
-      const C fs = f[a] - omega * (f[a] - feq) + Fa;
-      const int dxn = ex(a) > 0 ? xp : (ex(a) < 0 ? xm : x);
-      const int dyn = ey(a) > 0 ? yp : (ey(a) < 0 ? ym : y);
-      fb[a * N + (size_t)dyn * nx + dxn] = S(fs);
+      for (int i = 0; i < 4; ++i) {
+        const int a = i == 0 ? 1 : (i == 1 ? 2 : (i == 2 ? 5 : 6)), ab = opposite(a);
+        const C eu = (ex(a) ? C(ex(a)) * ux : C(0)) + (ey(a) ? C(ey(a)) * uy : C(0));
+        const C eF = (ex(a) ? C(ex(a)) * Fx : C(0)) + (ey(a) ? C(ey(a)) * Fy : C(0));
+        const C P = A0 + (o45 * eu + K3 * eF) * eu;
+        const C Q = o3 * eu + K * eF;
+        const C w = wgt<C>(a);
+        out[a] = one_m_omega * g[a] + w * (P + Q);
+        out[ab] = one_m_omega * g[ab] + w * (P - Q);
+      }
+      S st[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) st[a] = S(out[a]);
+      if constexpr (DEV) {
+        // The collision conserves mass exactly (sum of f_eq is rho, sum of the Guo term is 0),
+        // but rounding the nine FP32 results does not, and near a steady state the rounding
+        // repeats every step, so mass would drift linearly.  The rest population therefore
+        // takes the node's stored mass minus the eight rounded moving populations, written as
+        // g_0 + sum_a (g_a - g*_a) so that only small differences are added.
+        C d = C(0);
+#pragma unroll
+        for (int a = 1; a < 9; ++a) d += g[a] - C(st[a]);
+        st[0] = S(g[0] + d);
+      }
+      const int row = y * nx;
+      const int rowp = (y + 1 == ny ? 0 : y + 1) * nx, rowm = (y == 0 ? ny - 1 : y - 1) * nx;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const int dxn = ex(a) > 0 ? xp : (ex(a) < 0 ? xm : x);
+        const int drow = ey(a) > 0 ? rowp : (ey(a) < 0 ? rowm : row);
+        fb[a * N + drow + dxn] = st[a];
+      }
     }
   }
 }
@@ -210,8 +257,9 @@ template <typename S, int EOS>
 cudaError_t launch_t(const DevParams& p, const void* fa, void* fb, const uint8_t* flags,
                      double* rho_m, double* ux_m, double* uy_m, bool fields_only,
                      cudaStream_t s) {
-  dim3 block(TX, TY);
-  dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY);
+  constexpr int TH = TYT * StoreTraits<S>::RY;
+  dim3 block(TX, TYT);
+  dim3 grid((p.nx + TX - 1) / TX, (p.ny + TH - 1) / TH);
   if (fields_only)
     step_kernel<S, EOS, true><<<grid, block, 0, s>>>(p, (const S*)fa, (S*)fb, flags, rho_m, ux_m,
                                                       uy_m);

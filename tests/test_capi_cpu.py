@@ -52,6 +52,7 @@ def test_coexistence_rejects_supercritical():
     dict(scheme=lbm.FH, tau=1.0),                         # chi of Eq. (9) is singular
     dict(scheme=42),
     dict(nx=3),
+    dict(nx=16384, ny=16384),                             # 9 nx ny must stay below 2^31
     dict(circles=[(3.0, 50.0, 10.0)]),                    # crosses the periodic seam
     dict(circles=[(50.0, 50.0, -1.0)]),
     dict(eos=lbm.make_eos(lbm.EOS_CS, G=1.0, T_over_Tc=0.86)),  # CS needs G < 0
@@ -63,7 +64,7 @@ def test_create_rejects_invalid_arguments_before_touching_the_gpu(kw):
     args = dict(nx=100, ny=100, tau=1.0, scheme=lbm.HBB, circles=[(50.0, 35.0, 15.0)],
                 eos=lbm.make_eos(), precision=lbm.FP64)
     args.update(kw)
-    geo = lbm.make_geometry(args["nx"], 100, args["circles"])
+    geo = lbm.make_geometry(args["nx"], args.get("ny", 100), args["circles"])
     opt = lbm.Options()
     opt.precision = args["precision"]
     with pytest.raises(lbm.LBMError) as e:
