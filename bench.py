@@ -32,6 +32,26 @@ def bytes_per_update(precision):
     return 2 * 9 * (8 if precision == "fp64" else 4)
 
 
+def captured_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None when the
+    kernel source has changed since that capture."""
+    import hashlib
+    import re
+    summary = os.path.join(ROOT, "profiles", "step_kernel_fp32_dev_4096.md")
+    src = os.path.join(ROOT, "paper_1908_09235_gb300", "csrc", "step.cu")
+    if not os.path.exists(summary):
+        return None
+    text = open(summary).read()
+    m_sha = re.search(r"step.cu sha256 prefix: ([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    if not (m_sha and m_tr):
+        return None
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != m_sha.group(1):
+            return None
+    return int(m_tr.group(1))
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -276,11 +296,7 @@ def main():
     peak, peak_kind = measured_peaks()
     bpu = bytes_per_update("fp32_dev")
     achieved = n_fluid * bpu / (ms_step / args.steps * 1e-3) / 1e9
-    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-    traffic = None
-    if os.path.exists(traffic_file):
-        with open(traffic_file) as f:
-            traffic = json.load(f).get("step_kernel_fp32_dev_4096")
+    traffic = captured_traffic()
 
     variants = {}
     for prec in ("fp64", "fp32_dev"):
