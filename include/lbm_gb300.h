@@ -184,6 +184,28 @@ lbm_status lbm_links(lbm_ctx* ctx, int32_t* node, uint8_t* dir, double* q, int64
 
 lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
 
+/* Total mass of caller-owned device arrays without allocating any memory.  (This entry point
+ * has no counterpart in the paper; it serves callers that cannot allocate device memory: a host
+ * framework that already holds the device memory in its own pool, or a latency-critical loop
+ * that must not call cudaMalloc, which may synchronise the whole device.)
+ *   f           device array of 9*nx*ny populations [a][j][i]: FP64 values for LBM_FP64, FP32
+ *               values f_a - w_a rho_ref for LBM_FP32_DEV (the layout of this library)
+ *   flags       device array of nx*ny bytes, bit 0 = solid (skipped); NULL: every node is fluid
+ *   mass_out    device pointer: receives sum over fluid nodes of sum_a f_a (FP64, fixed order)
+ *   status_out  device pointer: receives LBM_OK, or LBM_EUNSTABLE if a fluid density is not
+ *               finite or not positive
+ *   stream      cudaStream_t the two kernels run on (asynchronously); NULL = legacy stream
+ * The reduction's scratch is a fixed device array of 2 x 8192 doubles (128 KiB) inside the
+ * library, held by every GPU that loads the library until the process exits; hence at most
+ * 8192 x 8192 = 67,108,864 nodes (larger lattices return LBM_EINVAL).  All calls on a device share
+ * that array: calls whose kernels overlap on the GPU race and give wrong results, so serialise
+ * them (e.g. one stream).  The first call on a device looks up the array's device address (no
+ * allocation) and should come before any stream capture.  Returns LBM_EINVAL for bad arguments,
+ * LBM_ECUDA if a launch fails; the mass and status arrive on the stream. */
+lbm_status lbm_mass_noalloc(const void* f, const uint8_t* flags, int32_t nx, int32_t ny,
+                            int32_t precision, double rho_ref, double* mass_out,
+                            int32_t* status_out, void* stream);
+
 /* Message of the sticky error, or "" when there is none.  Valid until the next call. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(lbm_status s);

@@ -28,7 +28,8 @@ STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM
 # Every entry point declared in include/lbm_gb300.h.
 EXPORTS = ("lbm_create", "lbm_coexistence", "lbm_init_fields", "lbm_init_droplet", "lbm_step",
            "lbm_step_timed", "lbm_mass", "lbm_fields", "lbm_fields_device", "lbm_flags",
-           "lbm_links", "lbm_info", "lbm_last_error", "lbm_status_string", "lbm_destroy")
+           "lbm_links", "lbm_info", "lbm_last_error", "lbm_status_string", "lbm_destroy",
+           "lbm_mass_noalloc")
 
 
 class LBMError(RuntimeError):
@@ -109,6 +110,8 @@ def load_library(build_if_missing=True):
             "lbm_last_error": (C.c_char_p, [P]),
             "lbm_status_string": (C.c_char_p, [C.c_int]),
             "lbm_destroy": (None, [P]),
+            "lbm_mass_noalloc": (C.c_int, [V, V, C.c_int32, C.c_int32, C.c_int32, C.c_double, V,
+                                           V, V]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
