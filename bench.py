@@ -137,6 +137,12 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def whole_job_mlups(world, fluid_nodes, steps, ms_max):
+    """Whole-job throughput of `world` replicas that each advanced `fluid_nodes` for `steps`
+    steps, timed by the slowest rank (ms_max)."""
+    return world * fluid_nodes * steps / (ms_max * 1e-3) / 1e6
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -292,7 +298,7 @@ def main():
     lat.close()
     ms_total = max_over_ranks(ms_total, world)
     n_fluid, n_all = info["n_fluid"], w.nx * w.ny
-    value = world * n_fluid * args.steps / (ms_total * 1e-3) / 1e6
+    value = whole_job_mlups(world, n_fluid, args.steps, ms_total)
     peak, peak_kind = measured_peaks()
     bpu = bytes_per_update("fp32_dev")
     achieved = n_fluid * bpu / (ms_step / args.steps * 1e-3) / 1e9

@@ -37,6 +37,7 @@ struct lbm_ctx {
   uint8_t* ldir = nullptr;
   double* lq = nullptr;
   double* carry = nullptr;
+  LinkRecipe recipe{};
   double* partials = nullptr;
   double* mass_out = nullptr;
   int* err_flag = nullptr;
@@ -123,8 +124,8 @@ lbm_status launch_one_step(lbm_ctx* c, cudaStream_t s, int cur) {
   cudaError_t e = launch_step(c->precision, c->p, fa, fb, c->flags, c->rho_m, c->ux_m, c->uy_m,
                               false, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
-  e = launch_boundary(c->precision, c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->lq, c->flags,
-                      fa, fb, c->rho_m, c->ux_m, c->uy_m, c->carry, s);
+  e = launch_boundary(c->precision, c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->recipe, fa,
+                      fb, c->rho_m, c->ux_m, c->uy_m, c->carry, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "boundary kernel launch");
   return LBM_OK;
 }
@@ -331,7 +332,7 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
   // ---- second allocation: boundary-link CSR and the FP64 rounding carry ----
   if (c->nb > 0) {
     size_t b2 = align_up(c->nb * 4) + align_up((c->nb + 1) * 4) + align_up(c->nl) +
-                align_up(c->nl * 8) + align_up(c->nb * 8);
+                align_up(c->nl * 8) + align_up(c->nb * 8) + align_up(link_recipe_bytes(c->nl));
     void* base2 = dev_alloc(c, b2);
     if (!base2) {
       release_all(c);
@@ -344,6 +345,7 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
     c->ldir = c2.take<uint8_t>(c->nl);
     c->lq = c2.take<double>(c->nl);
     c->carry = c2.take<double>(c->nb);
+    link_recipe_carve(c2.take<char>(link_recipe_bytes(c->nl)), c->nl, &c->recipe);
     if ((e = launch_geom_emit(g, c->flags, c->geom_tmp, c->bnode, c->boff, c->ldir, c->lq,
                               c->stream)) != cudaSuccess)
       return bail(e, "geom emit");
@@ -353,6 +355,9 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
       return bail(e, "copy boff");
     if ((e = cudaMemsetAsync(c->carry, 0, c->nb * 8, c->stream)) != cudaSuccess)
       return bail(e, "memset carry");
+    if ((e = launch_link_setup(c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->lq, c->flags,
+                               c->recipe, c->stream)) != cudaSuccess)
+      return bail(e, "link setup");
   }
   // fluid node count (host, once)
   std::vector<uint8_t> hf(N);
@@ -474,8 +479,8 @@ lbm_status lbm_step_timed(lbm_ctx* c, int32_t n, double* ms_step, double* ms_bnd
     if (e != cudaSuccess) st = cuda_fail(c, e, "step kernel launch");
     if (st == LBM_OK) cudaEventRecord(ev[2 * k + 1], c->stream);
     if (st == LBM_OK) {
-      e = launch_boundary(c->precision, c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->lq,
-                          c->flags, c->f[cur], c->f[1 - cur], c->rho_m, c->ux_m, c->uy_m, c->carry,
+      e = launch_boundary(c->precision, c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->recipe,
+                          c->f[cur], c->f[1 - cur], c->rho_m, c->ux_m, c->uy_m, c->carry,
                           c->stream);
       if (e != cudaSuccess) st = cuda_fail(c, e, "boundary kernel launch");
     }

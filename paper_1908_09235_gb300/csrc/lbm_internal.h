@@ -81,11 +81,32 @@ cudaError_t launch_step(int precision, const DevParams& p, const void* fa, void*
                         bool fields_only, cudaStream_t s);
 
 // boundary.cu
+// Per-link recipe of the wall pass, fixed at creation (depends on q, tau and the scheme only):
+//   f_abar(x_b, t+1) = c0 fo + c1 X1 + c2 X2 + chi rho' w_a [1 + 3 e.u_s + 4.5 (e.u_b)^2 - 1.5 u_b^2]
+// with fo = B[src], X1 = L1[x1], X2 = L2[x2] (element indices, -1 = unused; bit 0 of `kind`
+// selects lattice A for X2), u_s = cus u_b, or u(x_f) when uf >= 0.
+struct LinkRecipe {
+  int32_t* src;   // element index of the outgoing f*_a(x_b)
+  int32_t* dst;   // element index of the unknown f_abar(x_b)
+  int32_t* x1;
+  int32_t* x2;
+  int32_t* uf;    // node whose velocity is u_s (MLS, q < 1/2), or -1
+  uint8_t* kind;  // bit 0: X2 from lattice A;  bit 1: ghost term present (chi != 0 path)
+  double* c0;
+  double* c1;
+  double* c2;
+  double* chi;
+  double* cus;
+};
+size_t link_recipe_bytes(long long nl);
+void link_recipe_carve(char* base, long long nl, LinkRecipe* r);
+cudaError_t launch_link_setup(const DevParams& p, int nb, const int32_t* bnode,
+                              const int32_t* boff, const uint8_t* ldir, const double* lq,
+                              const uint8_t* flags, LinkRecipe r, cudaStream_t s);
 cudaError_t launch_boundary(int precision, const DevParams& p, int nb, const int32_t* bnode,
-                            const int32_t* boff, const uint8_t* ldir, const double* lq,
-                            const uint8_t* flags, const void* fa, void* fb, const double* rho_m,
-                            const double* ux_m, const double* uy_m, double* carry,
-                            cudaStream_t s);
+                            const int32_t* boff, const uint8_t* ldir, LinkRecipe r,
+                            const void* fa, void* fb, const double* rho_m, const double* ux_m,
+                            const double* uy_m, double* carry, cudaStream_t s);
 
 // ledger.cu
 int ledger_num_blocks(int N);
