@@ -29,7 +29,8 @@ SCHEME_NAMES = ("mls", "bouzidi_l", "zhao_yong", "mod_a", "mod_b")
 
 def bytes_per_update(precision):
     # algorithmic traffic of one fluid-node update: 9 populations read + 9 written
-    return 2 * 9 * (8 if precision == "fp64" else 4)
+    # (fp16_dev: the rest population in FP32, the eight moving ones in FP16)
+    return {"fp64": 144, "fp32_dev": 72, "fp16_dev": 40}[precision]
 
 
 def captured_traffic():
@@ -305,7 +306,7 @@ def main():
     traffic = captured_traffic()
 
     variants = {}
-    for prec in ("fp64", "fp32_dev"):
+    for prec in ("fp64", "fp32_dev", "fp16_dev"):
         for name in SCHEME_NAMES:
             s_ms, b_ms, t_ms, vinfo = time_variant(w, lbm.SCHEMES[name], lbm.PRECISIONS[prec],
                                                    args.variant_steps, 3)

@@ -60,10 +60,13 @@ typedef enum {
 } lbm_scheme;
 
 /* How populations are stored in device memory.  Arithmetic is FP64 for LBM_FP64 and FP32 for
- * the deviation formats, which store f_a - w_a rho_ref.  The boundary pass always computes in
- * FP64; with deviation storage its rounding residue is carried per boundary node in FP64 so the
- * mass-conserving schemes stay conserving. */
-typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 } lbm_precision;
+ * the deviation formats, which store f_a - w_a rho_ref: LBM_FP32_DEV all nine as FP32;
+ * LBM_FP16_DEV the rest population f_0 (which does not stream) as FP32 and the eight moving
+ * ones as FP16 (20 bytes per node and lattice).  In both the rest population takes the node's
+ * stored mass minus the rounded moving populations, so the bulk step keeps mass to FP32
+ * accuracy.  The boundary pass always computes in FP64; with deviation storage its rounding
+ * residue is carried per boundary node in FP64 so the mass-conserving schemes stay conserving. */
+typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1, LBM_FP16_DEV = 2 } lbm_precision;
 
 typedef enum { LBM_EOS_NONE = 0, LBM_EOS_EXP = 1, LBM_EOS_CS = 2 } lbm_eos_kind;
 
@@ -189,7 +192,8 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
  * framework that already holds the device memory in its own pool, or a latency-critical loop
  * that must not call cudaMalloc, which may synchronise the whole device.)
  *   f           device array of 9*nx*ny populations [a][j][i]: FP64 values for LBM_FP64, FP32
- *               values f_a - w_a rho_ref for LBM_FP32_DEV (the layout of this library)
+ *               values f_a - w_a rho_ref for LBM_FP32_DEV (the layout of this library);
+ *               LBM_FP16_DEV is not accepted
  *   flags       device array of nx*ny bytes, bit 0 = solid (skipped); NULL: every node is fluid
  *   mass_out    device pointer: receives sum over fluid nodes of sum_a f_a (FP64, fixed order)
  *   status_out  device pointer: receives LBM_OK, or LBM_EUNSTABLE if a fluid density is not

@@ -146,27 +146,25 @@ __global__ void link_setup_kernel(DevParams p, int nb, const int32_t* __restrict
 
 template <typename S>
 struct Lat {
-  const S* __restrict__ src;  // lattice A: f(t)
-  S* __restrict__ dst;        // lattice B: streamed values of step t
+  const void* __restrict__ src;  // lattice A: f(t)
+  void* __restrict__ dst;        // lattice B: streamed values of step t
+  int N;
   double rho_ref;
-  static constexpr bool dev = sizeof(S) == 4;
+  static constexpr bool dev = Pop<S>::dev;
   // value of element e of a plane with weight w (deviation formats store f - w rho_ref)
-  __device__ double load(const S* base, int e, double w) const {
-    double v = double(base[e]);
+  __device__ double load(const void* base, int e, double w) const {
+    double v = Pop<S>::load_e(base, e, N);
     if (dev) v += w * rho_ref;
     return v;
   }
   // store f at element e, returns the rounding residue (intended - stored) in FP64
   __device__ double store(int e, double w, double v) const {
     if (dev) {
-      double d = v - w * rho_ref;
-      S s = S(d);
-      dst[e] = s;
-      return d - double(s);
-    } else {
-      dst[e] = S(v);
-      return 0.0;
+      const double d = v - w * rho_ref;
+      return d - Pop<S>::store_e(dst, e, N, d);
     }
+    Pop<S>::store_e(dst, e, N, v);
+    return 0.0;
   }
 };
 
@@ -284,7 +282,7 @@ cudaError_t launch_b(const DevParams& p, int nb, const int32_t* bnode, const int
                      const uint8_t* ldir, LinkRecipe r, const void* fa, void* fb,
                      const double* rho_m, const double* ux_m, const double* uy_m, double* carry,
                      cudaStream_t s) {
-  Lat<S> L{(const S*)fa, (S*)fb, p.rho_ref};
+  Lat<S> L{fa, fb, p.N, p.rho_ref};
   const long long threads = 8LL * nb;
   boundary_kernel<S><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
       p, nb, bnode, boff, ldir, r, L, rho_m, ux_m, uy_m, carry);
@@ -334,6 +332,8 @@ cudaError_t launch_boundary(int precision, const DevParams& p, int nb, const int
   if (nb <= 0) return cudaSuccess;
   if (precision == LBM_FP32_DEV)
     return launch_b<float>(p, nb, bnode, boff, ldir, r, fa, fb, rho_m, ux_m, uy_m, carry, s);
+  if (precision == LBM_FP16_DEV)
+    return launch_b<__half>(p, nb, bnode, boff, ldir, r, fa, fb, rho_m, ux_m, uy_m, carry, s);
   return launch_b<double>(p, nb, bnode, boff, ldir, r, fa, fb, rho_m, ux_m, uy_m, carry, s);
 }
 

@@ -20,7 +20,7 @@ struct lbm_ctx {
   DevParams p{};
   GeomParams g{};
   int precision = LBM_FP64;
-  size_t pop_bytes = 8;
+  size_t lattice_bytes = 0;  // one lattice: 9 planes of nx*ny populations
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   lbm_alloc_fn alloc = nullptr;
@@ -195,7 +195,8 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
   if (scheme == LBM_FH && std::fabs(tau - 1.0) < 1e-3) return LBM_EINVAL;  // chi of Eq. (9)
   if (eos->kind < LBM_EOS_NONE || eos->kind > LBM_EOS_CS) return LBM_EINVAL;
   const int precision = opt ? opt->precision : LBM_FP64;
-  if (precision != LBM_FP64 && precision != LBM_FP32_DEV) return LBM_EINVAL;
+  if (precision != LBM_FP64 && precision != LBM_FP32_DEV && precision != LBM_FP16_DEV)
+    return LBM_EINVAL;
   if (opt && ((opt->alloc == nullptr) != (opt->free == nullptr))) return LBM_EINVAL;
   if (opt && opt->graph_steps < 0) return LBM_EINVAL;
   for (int k = 0; k < geo->n_circles; ++k) {
@@ -209,7 +210,11 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
 
   lbm_ctx* c = new lbm_ctx();
   c->precision = precision;
-  c->pop_bytes = precision == LBM_FP64 ? 8 : 4;
+  {
+    const size_t nn = (size_t)geo->nx * geo->ny;
+    // FP16: rest population as FP32, the eight moving ones as FP16
+    c->lattice_bytes = precision == LBM_FP64 ? 72 * nn : (precision == LBM_FP32_DEV ? 36 * nn : 20 * nn);
+  }
   c->stream = opt ? (cudaStream_t)opt->stream : nullptr;
   if (opt && opt->alloc) {
     c->alloc = opt->alloc;
@@ -283,7 +288,7 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
   const size_t N = (size_t)p.N;
   const int gblocks = geom_num_blocks(p.N);
   c->ledger_blocks = ledger_num_blocks(p.N);
-  size_t bytes = 2 * align_up(9 * N * c->pop_bytes) + align_up((N + 3) / 4 * 4) +
+  size_t bytes = 2 * align_up(c->lattice_bytes) + align_up((N + 3) / 4 * 4) +
                  3 * align_up(N * 8) + align_up(c->ledger_blocks * 8) + align_up(8) +
                  align_up(sizeof(int)) + align_up(gblocks * sizeof(int2)) + align_up(16);
   void* base = dev_alloc(c, bytes);
@@ -293,8 +298,8 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
     return LBM_ENOMEM;
   }
   Carver cv{(char*)base};
-  c->f[0] = cv.take<char>(9 * N * c->pop_bytes);
-  c->f[1] = cv.take<char>(9 * N * c->pop_bytes);
+  c->f[0] = cv.take<char>(c->lattice_bytes);
+  c->f[1] = cv.take<char>(c->lattice_bytes);
   c->flags = cv.take<uint8_t>((N + 3) / 4 * 4);
   c->rho_m = cv.take<double>(N);
   c->ux_m = cv.take<double>(N);
@@ -368,9 +373,9 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
   long long nf = 0;
   for (size_t k = 0; k < N; ++k) nf += (hf[k] & FLAG_SOLID) ? 0 : 1;
   c->n_fluid = nf;
-  if ((e = cudaMemsetAsync(c->f[0], 0, 9 * N * c->pop_bytes, c->stream)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(c->f[0], 0, c->lattice_bytes, c->stream)) != cudaSuccess)
     return bail(e, "memset f0");
-  if ((e = cudaMemsetAsync(c->f[1], 0, 9 * N * c->pop_bytes, c->stream)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(c->f[1], 0, c->lattice_bytes, c->stream)) != cudaSuccess)
     return bail(e, "memset f1");
   *out = c;
   return LBM_OK;
@@ -383,7 +388,6 @@ void lbm_destroy(lbm_ctx* c) {
 }
 
 static lbm_status init_common(lbm_ctx* c) {
-  const size_t N = (size_t)c->p.N;
   for (int k = 0; k < 2; ++k)  // kernel parameters (rho_ref) may have changed
     if (c->graph[k]) {
       cudaGraphExecDestroy(c->graph[k]);
@@ -391,7 +395,7 @@ static lbm_status init_common(lbm_ctx* c) {
     }
   LBM_CUDA(c, launch_init_eq(c->precision, c->p, c->flags, c->rho_m, c->ux_m, c->uy_m, c->f[0],
                              c->stream));
-  LBM_CUDA(c, cudaMemsetAsync(c->f[1], 0, 9 * N * c->pop_bytes, c->stream));
+  LBM_CUDA(c, cudaMemsetAsync(c->f[1], 0, c->lattice_bytes, c->stream));
   if (c->nb > 0) LBM_CUDA(c, cudaMemsetAsync(c->carry, 0, c->nb * 8, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->cur = 0;

@@ -1,5 +1,6 @@
 // Device-side D2Q9 lattice constants and the pseudopotential psi(rho).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lbm_internal.h"
@@ -33,6 +34,92 @@ __device__ __forceinline__ int wrap_any(int v, int n) {
   int r = v % n;
   return r < 0 ? r + n : r;
 }
+
+// Storage of the nine populations of a lattice.  Element (a, n) of plane a at node n:
+//   double  FP64 values, planes [a][n]
+//   float   FP32 deviations f_a - w_a rho_ref, planes [a][n]
+//   __half  mixed: plane 0 (the rest population, which never streams) as FP32 deviations, then
+//           planes 1..8 as FP16 deviations; the rest population absorbs the rounding of the
+//           moving ones, so mass stays at FP32 accuracy
+template <typename S>
+struct Pop;
+template <>
+struct Pop<double> {
+  using C = double;
+  static constexpr bool dev = false;
+  static __device__ __forceinline__ C load(const void* b, int a, int N, int n) {
+    return static_cast<const double*>(b)[a * N + n];
+  }
+  static __device__ __forceinline__ C rounded(int a, C v) { return v; }
+  static __device__ __forceinline__ void store(void* b, int a, int N, int n, C v) {
+    static_cast<double*>(b)[a * N + n] = v;
+  }
+  // element e = a N + n
+  static __device__ __forceinline__ double load_e(const void* b, int e, int N) {
+    return static_cast<const double*>(b)[e];
+  }
+  static __device__ __forceinline__ double store_e(void* b, int e, int N, double v) {
+    static_cast<double*>(b)[e] = v;
+    return v;
+  }
+};
+template <>
+struct Pop<float> {
+  using C = float;
+  static constexpr bool dev = true;
+  static __device__ __forceinline__ C load(const void* b, int a, int N, int n) {
+    return static_cast<const float*>(b)[a * N + n];
+  }
+  static __device__ __forceinline__ C rounded(int a, C v) { return v; }
+  static __device__ __forceinline__ void store(void* b, int a, int N, int n, C v) {
+    static_cast<float*>(b)[a * N + n] = v;
+  }
+  static __device__ __forceinline__ double load_e(const void* b, int e, int N) {
+    return double(static_cast<const float*>(b)[e]);
+  }
+  static __device__ __forceinline__ double store_e(void* b, int e, int N, double v) {
+    const float s = float(v);
+    static_cast<float*>(b)[e] = s;
+    return double(s);
+  }
+};
+template <>
+struct Pop<__half> {
+  using C = float;
+  static constexpr bool dev = true;
+  static __device__ __forceinline__ const __half* moving(const void* b, int N) {
+    return reinterpret_cast<const __half*>(static_cast<const float*>(b) + N);
+  }
+  static __device__ __forceinline__ __half* moving(void* b, int N) {
+    return reinterpret_cast<__half*>(static_cast<float*>(b) + N);
+  }
+  static __device__ __forceinline__ C load(const void* b, int a, int N, int n) {
+    return a == 0 ? static_cast<const float*>(b)[n] : __half2float(moving(b, N)[(a - 1) * N + n]);
+  }
+  static __device__ __forceinline__ C rounded(int a, C v) {
+    return a == 0 ? v : __half2float(__float2half_rn(v));
+  }
+  static __device__ __forceinline__ void store(void* b, int a, int N, int n, C v) {
+    if (a == 0)
+      static_cast<float*>(b)[n] = v;
+    else
+      moving(b, N)[(a - 1) * N + n] = __float2half_rn(v);
+  }
+  static __device__ __forceinline__ double load_e(const void* b, int e, int N) {
+    return e < N ? double(static_cast<const float*>(b)[e])
+                 : double(__half2float(moving(b, N)[e - N]));
+  }
+  static __device__ __forceinline__ double store_e(void* b, int e, int N, double v) {
+    if (e < N) {
+      const float s = float(v);
+      static_cast<float*>(b)[e] = s;
+      return double(s);
+    }
+    const __half h = __double2half(v);
+    moving(b, N)[e - N] = h;
+    return double(__half2float(h));
+  }
+};
 
 // psi(rho): exponential psi0 exp(-rho0/rho) (Sec. 3.2) or the Carnahan-Starling form
 // sqrt(2 (p - rho/3)/G); zero for a single-phase fluid.

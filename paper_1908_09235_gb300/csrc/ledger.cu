@@ -47,17 +47,16 @@ __device__ double block_sum(double v) {
 
 template <typename S>
 __global__ void __launch_bounds__(kLedgerThreads) mass_partial_kernel(
-    int N, double rho_ref, const S* __restrict__ f, const uint8_t* __restrict__ flags,
+    int N, double rho_ref, const void* __restrict__ f, const uint8_t* __restrict__ flags,
     double* __restrict__ partials, int* __restrict__ err) {
   Comp acc{0.0, 0.0};
   bool bad = false;
-  const size_t NN = (size_t)N;
   for (int n = blockIdx.x * kLedgerThreads + threadIdx.x; n < N; n += gridDim.x * kLedgerThreads) {
     if (flags[n] & FLAG_SOLID) continue;
     double r = 0.0;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) r += double(f[a * NN + n]);
-    if (sizeof(S) == 4) r += rho_ref;
+    for (int a = 0; a < 9; ++a) r += double(Pop<S>::load(f, a, N, n));
+    if (Pop<S>::dev) r += rho_ref;
     if (!(r > 0.0) || !isfinite(r)) bad = true;
     acc.add(r);
   }
@@ -78,12 +77,13 @@ __global__ void __launch_bounds__(kLedgerThreads) mass_final_kernel(const double
 template <typename S>
 __global__ void init_eq_kernel(DevParams p, const uint8_t* __restrict__ flags,
                                const double* __restrict__ rho, const double* __restrict__ ux,
-                               const double* __restrict__ uy, S* __restrict__ f) {
-  const size_t N = (size_t)p.N;
+                               const double* __restrict__ uy, void* __restrict__ f) {
+  using C = typename Pop<S>::C;
+  const int N = p.N;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < p.N; n += gridDim.x * blockDim.x) {
     if (flags[n] & FLAG_SOLID) {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) f[a * N + n] = S(0);
+      for (int a = 0; a < 9; ++a) Pop<S>::store(f, a, N, n, C(0));
       continue;
     }
     const double r = rho[n], u = ux[n], v = uy[n];
@@ -92,8 +92,8 @@ __global__ void init_eq_kernel(DevParams p, const uint8_t* __restrict__ flags,
     for (int a = 0; a < 9; ++a) {
       const double eu = ex(a) * u + ey(a) * v;
       double fe = wgt<double>(a) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);  // Eq. (4)
-      if (sizeof(S) == 4) fe -= wgt<double>(a) * p.rho_ref;
-      f[a * N + n] = S(fe);
+      if (Pop<S>::dev) fe -= wgt<double>(a) * p.rho_ref;
+      Pop<S>::store(f, a, N, n, C(fe));
     }
   }
 }
@@ -126,11 +126,14 @@ cudaError_t launch_mass(int precision, const DevParams& p, const void* f, const 
                         double* partials, int nblocks, double* result, int* err_flag,
                         cudaStream_t s) {
   if (precision == LBM_FP32_DEV)
-    mass_partial_kernel<float><<<nblocks, kLedgerThreads, 0, s>>>(p.N, p.rho_ref, (const float*)f,
-                                                                   flags, partials, err_flag);
+    mass_partial_kernel<float><<<nblocks, kLedgerThreads, 0, s>>>(p.N, p.rho_ref, f, flags,
+                                                                   partials, err_flag);
+  else if (precision == LBM_FP16_DEV)
+    mass_partial_kernel<__half><<<nblocks, kLedgerThreads, 0, s>>>(p.N, p.rho_ref, f, flags,
+                                                                    partials, err_flag);
   else
-    mass_partial_kernel<double><<<nblocks, kLedgerThreads, 0, s>>>(p.N, 0.0, (const double*)f,
-                                                                    flags, partials, err_flag);
+    mass_partial_kernel<double><<<nblocks, kLedgerThreads, 0, s>>>(p.N, 0.0, f, flags, partials,
+                                                                    err_flag);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   mass_final_kernel<<<1, kLedgerThreads, 0, s>>>(partials, nblocks, result);
@@ -141,9 +144,11 @@ cudaError_t launch_init_eq(int precision, const DevParams& p, const uint8_t* fla
                            const double* rho, const double* ux, const double* uy, void* f,
                            cudaStream_t s) {
   if (precision == LBM_FP32_DEV)
-    init_eq_kernel<float><<<grid_for(p.N), 256, 0, s>>>(p, flags, rho, ux, uy, (float*)f);
+    init_eq_kernel<float><<<grid_for(p.N), 256, 0, s>>>(p, flags, rho, ux, uy, f);
+  else if (precision == LBM_FP16_DEV)
+    init_eq_kernel<__half><<<grid_for(p.N), 256, 0, s>>>(p, flags, rho, ux, uy, f);
   else
-    init_eq_kernel<double><<<grid_for(p.N), 256, 0, s>>>(p, flags, rho, ux, uy, (double*)f);
+    init_eq_kernel<double><<<grid_for(p.N), 256, 0, s>>>(p, flags, rho, ux, uy, f);
   return cudaGetLastError();
 }
 

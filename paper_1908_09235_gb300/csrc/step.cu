@@ -10,7 +10,7 @@
 // A CTA covers a 32 x (8 RY) tile; each thread keeps the 9 populations of its RY nodes in
 // registers.  psi of the tile and of a one-node ring around it goes to shared memory (ring nodes
 // recompute their density from their own 9 populations), so the force needs no second pass over
-// memory.  RY = 4 rows per thread for FP32 storage, 2 for FP64 (register budget).
+// memory.  RY = 4 rows per thread for FP32 arithmetic, 2 for FP64 (register budget).
 #include "d2q9.cuh"
 
 namespace lbm {
@@ -21,18 +21,10 @@ constexpr int TX = 32;   // threads (and nodes) of a tile in x
 constexpr int TYT = 8;   // threads of a tile in y; each handles RY rows, TYT apart
 
 template <typename S>
-struct StoreTraits;
-template <>
-struct StoreTraits<double> {
-  using C = double;  // compute type
-  static constexpr bool deviation = false;
-  static constexpr int RY = 2;  // rows per thread (register budget of FP64)
-};
-template <>
-struct StoreTraits<float> {
-  using C = float;
-  static constexpr bool deviation = true;  // stores f_a - w_a rho_ref
-  static constexpr int RY = 4;
+struct StoreTraits {
+  using C = typename Pop<S>::C;  // compute type
+  static constexpr bool deviation = Pop<S>::dev;  // stores f_a - w_a rho_ref
+  static constexpr int RY = sizeof(C) == 8 ? 2 : 4;  // rows per thread (register budget)
 };
 
 // Sum of the nine stored values in direction order (a node's density, less rho_ref for the
@@ -47,8 +39,8 @@ __device__ __forceinline__ C pop_sum(const C (&f)[9]) {
 }
 
 template <typename S, int EOS, bool FIELDS>
-__global__ void __launch_bounds__(TX* TYT, sizeof(S) == 4 ? 4 : 2) step_kernel(DevParams p, const S* __restrict__ fa,
-                                                       S* __restrict__ fb,
+__global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 : 2)
+    step_kernel(DevParams p, const void* __restrict__ fa, void* __restrict__ fb,
                                                        const uint8_t* __restrict__ flags,
                                                        double* __restrict__ rho_m,
                                                        double* __restrict__ ux_m,
@@ -84,7 +76,7 @@ __global__ void __launch_bounds__(TX* TYT, sizeof(S) == 4 ? 4 : 2) step_kernel(D
     rho[r] = C(1);
     if (!(fl[r] & FLAG_SOLID)) {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) f[r][a] = C(fa[a * N + n]);
+      for (int a = 0; a < 9; ++a) f[r][a] = Pop<S>::load(fa, a, N, n);
     } else {
 #pragma unroll
       for (int a = 0; a < 9; ++a) f[r][a] = C(0);
@@ -121,7 +113,7 @@ __global__ void __launch_bounds__(TX* TYT, sizeof(S) == 4 ? 4 : 2) step_kernel(D
       ring_fluid = !(flags[m] & FLAG_SOLID);
       if (ring_fluid) {
 #pragma unroll
-        for (int a = 0; a < 9; ++a) v[a] = C(fa[a * N + m]);
+        for (int a = 0; a < 9; ++a) v[a] = Pop<S>::load(fa, a, N, m);
       }
     }
 #pragma unroll
@@ -227,9 +219,9 @@ __global__ void __launch_bounds__(TX* TYT, sizeof(S) == 4 ? 4 : 2) step_kernel(D
         out[a] = one_m_omega * g[a] + w * (P + Q);
         out[ab] = one_m_omega * g[ab] + w * (P - Q);
       }
-      S st[9];
+      C st[9];  // the values as stored (rounded to the storage format)
 #pragma unroll
-      for (int a = 0; a < 9; ++a) st[a] = S(out[a]);
+      for (int a = 0; a < 9; ++a) st[a] = Pop<S>::rounded(a, out[a]);
       if constexpr (DEV) {
         // The collision conserves mass exactly (sum of f_eq is rho, sum of the Guo term is 0),
         // but rounding the nine FP32 results does not, and near a steady state the rounding
@@ -238,8 +230,8 @@ __global__ void __launch_bounds__(TX* TYT, sizeof(S) == 4 ? 4 : 2) step_kernel(D
         // g_0 + sum_a (g_a - g*_a) so that only small differences are added.
         C d = C(0);
 #pragma unroll
-        for (int a = 1; a < 9; ++a) d += g[a] - C(st[a]);
-        st[0] = S(g[0] + d);
+        for (int a = 1; a < 9; ++a) d += g[a] - st[a];
+        st[0] = g[0] + d;
       }
       const int row = y * nx;
       const int rowp = (y + 1 == ny ? 0 : y + 1) * nx, rowm = (y == 0 ? ny - 1 : y - 1) * nx;
@@ -247,7 +239,7 @@ __global__ void __launch_bounds__(TX* TYT, sizeof(S) == 4 ? 4 : 2) step_kernel(D
       for (int a = 0; a < 9; ++a) {
         const int dxn = ex(a) > 0 ? xp : (ex(a) < 0 ? xm : x);
         const int drow = ey(a) > 0 ? rowp : (ey(a) < 0 ? rowm : row);
-        fb[a * N + drow + dxn] = st[a];
+        Pop<S>::store(fb, a, N, drow + dxn, st[a]);
       }
     }
   }
@@ -261,11 +253,9 @@ cudaError_t launch_t(const DevParams& p, const void* fa, void* fb, const uint8_t
   dim3 block(TX, TYT);
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + TH - 1) / TH);
   if (fields_only)
-    step_kernel<S, EOS, true><<<grid, block, 0, s>>>(p, (const S*)fa, (S*)fb, flags, rho_m, ux_m,
-                                                      uy_m);
+    step_kernel<S, EOS, true><<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m);
   else
-    step_kernel<S, EOS, false><<<grid, block, 0, s>>>(p, (const S*)fa, (S*)fb, flags, rho_m,
-                                                       ux_m, uy_m);
+    step_kernel<S, EOS, false><<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m);
   return cudaGetLastError();
 }
 
@@ -290,6 +280,8 @@ cudaError_t launch_step(int precision, const DevParams& p, const void* fa, void*
                         bool fields_only, cudaStream_t s) {
   if (precision == LBM_FP32_DEV)
     return launch_s<float>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
+  if (precision == LBM_FP16_DEV)
+    return launch_s<__half>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
   return launch_s<double>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
 }
 

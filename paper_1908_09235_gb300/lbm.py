@@ -19,8 +19,8 @@ SCHEMES = {
     "zhao_yong": ZHAO_YONG, "mod_a": MOD_A, "mod_b": MOD_B, "bao": BAO,
     "bouzidi_l_a": BOUZIDI_L_A,
 }
-FP64, FP32_DEV = 0, 1
-PRECISIONS = {"fp64": FP64, "fp32_dev": FP32_DEV}
+FP64, FP32_DEV, FP16_DEV = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32_dev": FP32_DEV, "fp16_dev": FP16_DEV}
 EOS_NONE, EOS_EXP, EOS_CS = 0, 1, 2
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EUNSTABLE",
           5: "LBM_ETIMEOUT", 6: "LBM_ESTATE"}

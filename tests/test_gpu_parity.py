@@ -25,6 +25,11 @@ TOL64 = 1e-11
 # ~2e-5 normwise / ~4e-5 pointwise (vapour, rho_V = 0.034) after 1000.
 #   100 steps:  max |d rho| / max rho <= 1e-5
 #   1000 steps: max |d rho| / max rho <= 5e-5 and max |d rho| / rho <= 1e-4
+# FP16 moving populations: each stored population carries one FP16 rounding (2^-11 = 4.9e-4
+# relative), so after 100 steps the normwise error is about one FP16 unit (measured 3.7-4.2e-4);
+# like the FP32 rounding it repeats near a steady state and grows to 0.6-3.8e-3 after 1000 steps.
+TOL16_NORM_100 = 2e-3
+TOL16_NORM_1000 = 1e-2
 TOL32_NORM_100 = 1e-5
 TOL32_NORM_1000 = 5e-5
 TOL32_POINT_1000 = 1e-4
@@ -225,8 +230,31 @@ def test_droplet_on_cylinder_fp32_dev(gpu_lib, scheme):
     lat.close()
 
 
+# ---- FP16 moving populations (rest population FP32), FP32 arithmetic --------------------------
+@pytest.mark.parametrize("scheme", [lbm.MOD_A, lbm.MOD_B, lbm.MLS])
+def test_droplet_on_cylinder_fp16_dev(gpu_lib, scheme):
+    case = c0_case()
+    lat = case.gpu(scheme, precision=lbm.FP16_DEV)
+    s = case.oracle(scheme)
+    m0 = lat.mass()
+    lat.step(100)
+    s.step(100)
+    norm100, point100 = _fp32_errors(lat, s)
+    lat.step(900)
+    s.step(900)
+    norm, point = _fp32_errors(lat, s)
+    print("fp16_dev scheme %d: rho error normwise %.3e (100 steps) %.3e (1000), pointwise %.3e "
+          "(100) %.3e (1000)" % (scheme, norm100, norm, point100, point))
+    assert norm100 <= TOL16_NORM_100, norm100
+    assert norm <= TOL16_NORM_1000, norm
+    if scheme in (lbm.MOD_A, lbm.MOD_B):
+        # the FP32 rest population absorbs the FP16 rounding of the moving populations
+        assert abs(lat.mass() / m0 - 1) < 1e-6
+    lat.close()
+
+
 # ---- full size (4096^2, the benchmark's launch configuration): all nodes after a few steps -----
-@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_DEV])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_DEV, lbm.FP16_DEV])
 def test_large_droplet_on_cylinder_full_size(gpu_lib, precision):
     w = workloads.LARGE
     case = Case(w.nx, w.ny, w.tau, "cs", circles=w.circles, init=("droplet",) + tuple(w.drop))
@@ -246,5 +274,7 @@ def test_large_droplet_on_cylinder_full_size(gpu_lib, precision):
     else:
         m = np.isfinite(o[0])
         rel = float(np.max(np.abs(g[0][m] - o[0][m]) / o[0][m]))
-        assert rel <= TOL32_NORM_100, rel  # three steps
+        print("full size, precision %d, 3 steps: pointwise rho error %.3e" % (precision, rel))
+        tol = TOL32_NORM_100 if precision == lbm.FP32_DEV else TOL16_NORM_100
+        assert rel <= tol, rel  # three steps
     lat.close()
