@@ -210,6 +210,62 @@ lbm_status lbm_mass_noalloc(const void* f, const uint8_t* flags, int32_t nx, int
                             int32_t precision, double rho_ref, double* mass_out,
                             int32_t* status_out, void* stream);
 
+/* ---- Batches: many lattices advanced together -------------------------------------------------
+ * A batch holds up to max_domains lattices of one precision and one EOS kind.  One batch step is
+ * three kernel launches for all of them (a persistent step kernel over a table of tiles, a
+ * persistent boundary kernel over all boundary nodes, and a kernel that advances each lattice's
+ * state), replayed from a CUDA graph; lattices join and leave between steps and each stops at its
+ * own step budget.  A lattice gives the same bits alone (lbm_step) and inside any batch. */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct {
+  lbm_geometry geometry;
+  lbm_eos eos;
+  double tau;
+  int32_t scheme;   /* lbm_scheme */
+  int32_t init;     /* 1: droplet (cx, cy, R, W, rho_in, rho_out); 0: rho = rho_in, u = 0 */
+  double cx, cy, R, W, rho_in, rho_out;
+} lbm_domain;
+
+typedef struct {
+  int32_t active;          /* lattices in the batch                                         */
+  int32_t tiles;           /* tiles in the current table (-1 before the first step)         */
+  int32_t tile_rows, tile_cols;
+  int64_t nodes, fluid_nodes, boundary_links;
+  int64_t device_bytes;    /* device memory of the batch and its lattices                   */
+} lbm_batch_info_t;
+
+/* opt: stream and allocation hook for the batch and every lattice in it (precision is taken
+ * from the argument).  LBM_EINVAL for bad arguments. */
+lbm_status lbm_batch_create(int32_t precision, int32_t eos_kind, int32_t max_domains,
+                            const lbm_options* opt, lbm_batch** out);
+/* Create, initialise and add a lattice with a budget of `steps` time steps; *slot receives its
+ * index.  LBM_ENOMEM when no slot or no device memory is free (nothing is added), LBM_EINVAL
+ * when d->eos.kind differs from the batch's. */
+lbm_status lbm_batch_add(lbm_batch* b, const lbm_domain* d, int64_t steps, int32_t* slot);
+lbm_status lbm_batch_remove(lbm_batch* b, int32_t slot);          /* frees its memory */
+lbm_status lbm_batch_set_steps(lbm_batch* b, int32_t slot, int64_t steps); /* new budget */
+/* Advance every lattice by n steps or until its budget is spent (asynchronous). */
+lbm_status lbm_batch_step(lbm_batch* b, int32_t n);
+/* As lbm_batch_step without graphs, with CUDA events around each kernel; blocks and returns
+ * the total time and the summed times of the step kernel and of boundary + advance kernels. */
+lbm_status lbm_batch_step_timed(lbm_batch* b, int32_t n, double* ms_total, double* ms_step_kernel,
+                                double* ms_boundary);
+/* Steps done and left of a lattice (blocks). */
+lbm_status lbm_batch_progress(lbm_batch* b, int32_t slot, int64_t* steps_done,
+                              int64_t* steps_left);
+/* The lattice's context, current as of this call, for lbm_mass, lbm_fields, lbm_info (blocks).
+ * It stays owned by the batch; do not step or destroy it directly. */
+lbm_status lbm_batch_domain(lbm_batch* b, int32_t slot, lbm_ctx** ctx);
+/* Time the step kernel for each tile height (8, 16, 32 rows; FP64: 8, 16) on the current batch
+ * without changing any state, keep the fastest; *tile_rows receives it. */
+lbm_status lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* tile_rows);
+lbm_status lbm_batch_info(lbm_batch* b, lbm_batch_info_t* out);
+/* Device bytes a lattice would need in a batch of the given precision (upper estimate). */
+lbm_status lbm_domain_bytes(const lbm_domain* d, int32_t precision, int64_t* bytes);
+const char* lbm_batch_last_error(const lbm_batch* b);
+void lbm_batch_destroy(lbm_batch* b);
+
 /* Message of the sticky error, or "" when there is none.  Valid until the next call. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(lbm_status s);

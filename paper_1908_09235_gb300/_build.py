@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["step.cu", "boundary.cu", "geometry.cu", "ledger.cu", "capi.cu", "mass_noalloc.cu"]
+CUDA_SOURCES = ["step.cu", "boundary.cu", "geometry.cu", "ledger.cu", "capi.cu", "batch.cu",
+                "mass_noalloc.cu"]
 CXX_SOURCES = ["eos_host.cpp"]
 
 
@@ -49,7 +50,11 @@ def build(force=False, verbose=False):
     procs = []
     for src in CUDA_SOURCES:
         obj = os.path.join(objdir, src + ".o")
-        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+        # The wall pass is compiled without multiply-add contraction: its per-link arithmetic is
+        # inlined into the single-lattice and the batched kernels, and must round identically in
+        # both so a lattice gives the same bits alone and in a batch.
+        fmad = ["--fmad=false"] if src == "boundary.cu" else []
+        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", *fmad, "-Xcompiler", "-fPIC",
                "-Xcompiler", "-ffp-contract=off", "-c", os.path.join(CSRC, src), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     cuda_inc = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include")

@@ -28,10 +28,11 @@ constexpr uint8_t kFromA = 1;   // X2 is read from lattice A (pre-collision)
 constexpr uint8_t kGhost = 2;   // the link has the ghost-node term chi f_eq(x_s)
 
 // The bracket of Eqs. (8), (20), (22): w_a [1 + 3 e_a.u_s + 4.5 (e_a.u_b)^2 - 1.5 u_b.u_b].
-__device__ __forceinline__ double bracket(int a, double usx, double usy, double ubx, double uby) {
-  double eus = ex(a) * usx + ey(a) * usy;
-  double eub = ex(a) * ubx + ey(a) * uby;
-  return wgt<double>(a) * (1.0 + 3.0 * eus + 4.5 * eub * eub - 1.5 * (ubx * ubx + uby * uby));
+template <typename T>
+__device__ __forceinline__ T bracket(int a, T usx, T usy, T ubx, T uby) {
+  const T eus = T(ex(a)) * usx + T(ey(a)) * usy;
+  const T eub = T(ex(a)) * ubx + T(ey(a)) * uby;
+  return wgt<T>(a) * (T(1) + T(3) * eus + T(4.5) * eub * eub - T(1.5) * (ubx * ubx + uby * uby));
 }
 
 // One thread per boundary node: the recipe of each of its links.
@@ -141,6 +142,11 @@ __global__ void link_setup_kernel(DevParams p, int nb, const int32_t* __restrict
     r.c2[l] = c2;
     r.chi[l] = chi;
     r.cus[l] = cus;
+    r.c0f[l] = float(c0);
+    r.c1f[l] = float(c1);
+    r.c2f[l] = float(c2);
+    r.chif[l] = float(chi);
+    r.cusf[l] = float(cus);
   }
 }
 
@@ -150,30 +156,148 @@ struct Lat {
   void* __restrict__ dst;        // lattice B: streamed values of step t
   int N;
   double rho_ref;
-  static constexpr bool dev = Pop<S>::dev;
-  // value of element e of a plane with weight w (deviation formats store f - w rho_ref)
-  __device__ double load(const void* base, int e, double w) const {
-    double v = Pop<S>::load_e(base, e, N);
-    if (dev) v += w * rho_ref;
-    return v;
-  }
-  // store f at element e, returns the rounding residue (intended - stored) in FP64
-  __device__ double store(int e, double w, double v) const {
-    if (dev) {
-      const double d = v - w * rho_ref;
-      return d - Pop<S>::store_e(dst, e, N, d);
-    }
-    Pop<S>::store_e(dst, e, N, v);
-    return 0.0;
-  }
 };
 
-// Sum over the 8 lanes of a node's group in a fixed tree order (bitwise reproducible).
-__device__ __forceinline__ double group8_sum(double v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 4);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
+// Sum over the 8 lanes of a node's group in a fixed tree order (bitwise reproducible); `mask`
+// holds the 8 lanes of the group.
+template <typename T>
+__device__ __forceinline__ T group8_sum(T v, unsigned mask) {
+  v += __shfl_xor_sync(mask, v, 4);
+  v += __shfl_xor_sync(mask, v, 2);
+  v += __shfl_xor_sync(mask, v, 1);
   return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T pick(const double* d, const float* f, int l) {
+  if constexpr (sizeof(T) == 8) return d[l]; else return f[l];
+}
+
+// Boundary node b of a lattice handled by lane k (0..7) of an 8-lane group (node_ok false: a
+// padding group, which still takes part in the shuffles).  Arithmetic type T: FP64 for FP64
+// storage; FP32 for the deviation formats, whose mass bookkeeping is exact instead: each node's
+// imbalance between the stored outgoing and incoming values is summed in FP64 and goes, with the
+// previous step's FP64 rounding residue, into its rest population.  For schemes A and
+// L-Bouzidi + A that is Eq. (18); for B (balanced by construction, Eq. 19) and halfway
+// bounce-back it only returns the FP32 rounding.
+template <typename S>
+__device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k, bool node_ok,
+                                               const int32_t* __restrict__ bnode,
+                                               const int32_t* __restrict__ boff,
+                                               const uint8_t* __restrict__ ldir,
+                                               const LinkRecipe& r, const Lat<S>& L,
+                                               const double* __restrict__ rho_m,
+                                               const double* __restrict__ ux_m,
+                                               const double* __restrict__ uy_m,
+                                               double* __restrict__ carry, unsigned mask) {
+  using T = typename Pop<S>::C;
+  constexpr bool DEV = Pop<S>::dev;
+  const int scheme = p.scheme;
+  const int N = L.N;
+  const bool fix_f0 = scheme == LBM_MOD_A || scheme == LBM_BOUZIDI_L_A;
+  const bool conserving = fix_f0 || scheme == LBM_MOD_B || scheme == LBM_HBB;
+  const bool fict = scheme == LBM_MOD_B || scheme == LBM_BAO;
+  const T rref = DEV ? p.k<T>().rho_ref : T(0);
+  // macro arrays: FP64 for FP64 storage, FP32 (in the same memory) for the deviation formats
+  const T* rhoT = reinterpret_cast<const T*>(rho_m);
+  const T* uxT = reinterpret_cast<const T*>(ux_m);
+  const T* uyT = reinterpret_cast<const T*>(uy_m);
+
+  // round 1: node and link records
+  int n = 0, l0 = 0, nl = 0;
+  if (node_ok) {
+    n = bnode[b];
+    l0 = boff[b];
+    nl = boff[b + 1] - l0;
+  }
+  const bool act = node_ok && k < nl;
+  int a = 1, src = 0, dst = 0, x1 = -1, x2 = -1, uf = -1;
+  uint8_t kind = 0;
+  T c0 = T(1), c1 = T(0), c2 = T(0), chi = T(0), cus = T(0);
+  T rho_b = T(1), ubx = T(0), uby = T(0);
+  if (act) {
+    const int l = l0 + k;
+    a = ldir[l];
+    src = r.src[l];
+    dst = r.dst[l];
+    x1 = r.x1[l];
+    x2 = r.x2[l];
+    uf = r.uf[l];
+    kind = r.kind[l];
+    c0 = pick<T>(r.c0, r.c0f, l);
+    c1 = pick<T>(r.c1, r.c1f, l);
+    c2 = pick<T>(r.c2, r.c2f, l);
+    chi = pick<T>(r.chi, r.chif, l);
+    cus = pick<T>(r.cus, r.cusf, l);
+    rho_b = rhoT[n];
+    ubx = uxT[n];
+    uby = uyT[n];
+  }
+  // round 2: lattice values (deviations d_ for the FP32 formats; f = d_ + w rho_ref)
+  const T w = wgt<T>(a);
+  const T wr = w * rref;
+  T fo_d = T(0), X1 = T(0), X2 = T(0), usx = T(0), usy = T(0);
+  if (act) {
+    fo_d = Pop<S>::load_t(L.dst, src, N);  // outgoing f*_a(x_b, t)
+    if (x1 >= 0) X1 = Pop<S>::load_t(L.dst, x1, N) + wr;
+    if (x2 >= 0) X2 = Pop<S>::load_t((kind & kFromA) ? L.src : L.dst, x2, N) + wr;
+    if (kind & kGhost) {
+      if (uf >= 0) {
+        usx = uxT[uf];
+        usy = uyT[uf];
+      } else {
+        usx = cus * ubx;
+        usy = cus * uby;
+      }
+    }
+  }
+  const T fo = fo_d + wr;
+  const bool lane0 = node_ok && k == 0;
+  T f0_d = T(0);
+  if (lane0 && (fix_f0 || (DEV && conserving))) f0_d = Pop<S>::load_t(L.dst, n, N);
+
+  const bool gh = act && (kind & kGhost);
+  const T br = gh ? bracket<T>(a, usx, usy, ubx, uby) : T(0);
+  T rho_s = rho_b;
+  if (fict) {
+    T num = T(0), den = T(0);
+    if (gh) {  // links without a ghost term are halfway bounce-back: chi = 0
+      num = scheme == LBM_MOD_B ? chi * fo : fo;  // Eq. (22) / Eq. (23)
+      den = scheme == LBM_MOD_B ? chi * br : br;
+    }
+    num = group8_sum(num, mask);
+    den = group8_sum(den, mask);
+    if (den != T(0)) rho_s = num / den;
+  }
+  T val = c0 * fo + c1 * X1 + c2 * X2;
+  if (gh) val += chi * ((fict ? rho_s : rho_b) * br);  // Eq. (8) / Eq. (20) in Eq. (7) / (17)
+  T in_d = T(0);
+  if (act) {
+    // a pure bounce-back link (halfway bounce-back or a fallback) copies the stored value
+    const bool copy = DEV && !gh && x1 < 0 && x2 < 0 && c0 == T(1);
+    in_d = Pop<S>::store_t(L.dst, dst, N, copy ? fo_d : val - wr);
+  }
+
+  if constexpr (DEV) {
+    if (conserving) {
+      // exact FP64 imbalance of the stored deviations (the w rho_ref parts cancel)
+      const double dm = group8_sum(act ? double(fo_d) - double(in_d) : 0.0, mask);
+      if (lane0) {
+        const double want = double(f0_d) + dm + carry[b];
+        if (want != double(f0_d)) {
+          const T st = Pop<S>::store_t(L.dst, n, N, T(want));
+          carry[b] = want - double(st);
+        } else {
+          carry[b] = 0.0;
+        }
+      }
+    }
+  } else {
+    if (fix_f0) {
+      const double dm = group8_sum(act ? fo - val : 0.0, mask);  // Eq. (15)
+      if (lane0) Pop<S>::store_t(L.dst, n, N, f0_d + dm);     // Eq. (18)
+    }
+  }
 }
 
 template <typename S>
@@ -187,93 +311,38 @@ __global__ void __launch_bounds__(128) boundary_kernel(DevParams p, int nb,
                                                        const double* __restrict__ uy_m,
                                                        double* __restrict__ carry) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = gt >> 3, k = gt & 7;
-  const bool node_ok = b < nb;
-  const int scheme = p.scheme;
-  const bool fix_f0 = scheme == LBM_MOD_A || scheme == LBM_BOUZIDI_L_A;
-  const bool conserving = fix_f0 || scheme == LBM_MOD_B || scheme == LBM_HBB;
-  const bool fict = scheme == LBM_MOD_B || scheme == LBM_BAO;
+  const int b = gt >> 3;
+  boundary_group<S>(p, b, gt & 7, b < nb, bnode, boff, ldir, r, L, rho_m, ux_m, uy_m, carry,
+                    0xffffffffu);
+}
 
-  // round 1: node and link records
-  int n = 0, l0 = 0, nl = 0;
-  if (node_ok) {
-    n = bnode[b];
-    l0 = boff[b];
-    nl = boff[b + 1] - l0;
+// Boundary nodes of many lattices: items are (domain, boundary node); a persistent grid of
+// 8-lane groups walks them.  Lattices whose step budget is spent are skipped.
+template <typename S>
+__global__ void __launch_bounds__(128) batch_boundary_kernel(const BatchDomain* __restrict__ doms,
+                                                             const int2* __restrict__ items,
+                                                             const int* __restrict__ n_items) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = gt & 7;
+  const unsigned mask = 0xffu << (threadIdx.x & 24);
+  const int ni = *n_items;
+  for (int i = gt >> 3; i < ni; i += (gridDim.x * blockDim.x) >> 3) {
+    const int2 it = items[i];
+    const BatchDomain& D = doms[it.x];
+    if (D.steps_left <= 0) continue;  // uniform over the group
+    const int cur = D.cur;
+    const Lat<S> L{D.f[cur], D.f[cur ^ 1], D.p.N, D.p.rho_ref};
+    boundary_group<S>(D.p, it.y, k, true, D.bnode, D.boff, D.ldir, D.recipe, L, D.rho_m, D.ux_m,
+                      D.uy_m, D.carry, mask);
   }
-  const bool act = node_ok && k < nl;
-  int a = 1, src = 0, dst = 0, x1 = -1, x2 = -1, uf = -1;
-  uint8_t kind = 0;
-  double c0 = 1.0, c1 = 0.0, c2 = 0.0, chi = 0.0, cus = 0.0;
-  double rho_b = 1.0, ubx = 0.0, uby = 0.0;
-  if (act) {
-    const int l = l0 + k;
-    a = ldir[l];
-    src = r.src[l];
-    dst = r.dst[l];
-    x1 = r.x1[l];
-    x2 = r.x2[l];
-    uf = r.uf[l];
-    kind = r.kind[l];
-    c0 = r.c0[l];
-    c1 = r.c1[l];
-    c2 = r.c2[l];
-    chi = r.chi[l];
-    cus = r.cus[l];
-    rho_b = rho_m[n];
-    ubx = ux_m[n];
-    uby = uy_m[n];
-  }
-  // round 2: lattice values
-  const double w = wgt<double>(a);
-  double fo = 0.0, X1 = 0.0, X2 = 0.0, usx = 0.0, usy = 0.0;
-  if (act) {
-    fo = L.load(L.dst, src, w);  // outgoing f*_a(x_b, t)
-    if (x1 >= 0) X1 = L.load(L.dst, x1, w);
-    if (x2 >= 0) X2 = L.load((kind & kFromA) ? L.src : L.dst, x2, w);
-    if (kind & kGhost) {
-      if (uf >= 0) {
-        usx = ux_m[uf];
-        usy = uy_m[uf];
-      } else {
-        usx = cus * ubx;
-        usy = cus * uby;
-      }
-    }
-  }
-  double f0_old = 0.0;
-  if (node_ok && k == 0 && (fix_f0 || (L.dev && conserving))) f0_old = L.load(L.dst, n, wgt<double>(0));
+}
 
-  const bool gh = act && (kind & kGhost);
-  const double br = gh ? bracket(a, usx, usy, ubx, uby) : 0.0;
-  double rho_s = rho_b;
-  if (fict) {
-    double num = 0.0, den = 0.0;
-    if (gh) {  // links without a ghost term are halfway bounce-back: chi = 0
-      num = scheme == LBM_MOD_B ? chi * fo : fo;  // Eq. (22) / Eq. (23)
-      den = scheme == LBM_MOD_B ? chi * br : br;
-    }
-    num = group8_sum(num);
-    den = group8_sum(den);
-    if (den != 0.0) rho_s = num / den;
-  }
-  double val = c0 * fo + c1 * X1 + c2 * X2;
-  if (gh) val += chi * ((fict ? rho_s : rho_b) * br);  // Eq. (8) / Eq. (20) in Eq. (7) / (17)
-  double resid = 0.0;
-  if (act) resid = L.store(dst, w, val);
-
-  double dm = 0.0;
-  if (fix_f0) dm = group8_sum(act ? fo - val : 0.0);  // Eq. (15)
-  if (L.dev && conserving) resid = group8_sum(resid);
-  if (node_ok && k == 0) {
-    if (fix_f0) {
-      double f0 = f0_old + dm;  // Eq. (18)
-      if (L.dev) f0 += carry[b];
-      resid += L.store(n, wgt<double>(0), f0);
-    } else if (L.dev && conserving && carry[b] != 0.0) {
-      resid += L.store(n, wgt<double>(0), f0_old + carry[b]);
-    }
-    if (L.dev && conserving) carry[b] = resid;
+__global__ void batch_advance_kernel(BatchDomain* __restrict__ doms, int n) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d < n && doms[d].steps_left > 0) {
+    doms[d].cur ^= 1;
+    --doms[d].steps_left;
+    ++doms[d].steps_done;
   }
 }
 
@@ -282,7 +351,7 @@ cudaError_t launch_b(const DevParams& p, int nb, const int32_t* bnode, const int
                      const uint8_t* ldir, LinkRecipe r, const void* fa, void* fb,
                      const double* rho_m, const double* ux_m, const double* uy_m, double* carry,
                      cudaStream_t s) {
-  Lat<S> L{fa, fb, p.N, p.rho_ref};
+  Lat<S> L{fa, fb, p.N, p.rho_ref};  // rho_ref also in p.k<T>() for the FP32 formats
   const long long threads = 8LL * nb;
   boundary_kernel<S><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
       p, nb, bnode, boff, ldir, r, L, rho_m, ux_m, uy_m, carry);
@@ -294,7 +363,7 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 }  // namespace
 
 size_t link_recipe_bytes(long long nl) {
-  return 5 * align256(nl * 4) + align256(nl) + 5 * align256(nl * 8);
+  return 5 * align256(nl * 4) + align256(nl) + 5 * align256(nl * 8) + 5 * align256(nl * 4);
 }
 
 void link_recipe_carve(char* base, long long nl, LinkRecipe* r) {
@@ -315,6 +384,11 @@ void link_recipe_carve(char* base, long long nl, LinkRecipe* r) {
   r->c2 = (double*)take(nl * 8);
   r->chi = (double*)take(nl * 8);
   r->cus = (double*)take(nl * 8);
+  r->c0f = (float*)take(nl * 4);
+  r->c1f = (float*)take(nl * 4);
+  r->c2f = (float*)take(nl * 4);
+  r->chif = (float*)take(nl * 4);
+  r->cusf = (float*)take(nl * 4);
 }
 
 cudaError_t launch_link_setup(const DevParams& p, int nb, const int32_t* bnode,
@@ -322,6 +396,23 @@ cudaError_t launch_link_setup(const DevParams& p, int nb, const int32_t* bnode,
                               const uint8_t* flags, LinkRecipe r, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   link_setup_kernel<<<(nb + 127) / 128, 128, 0, s>>>(p, nb, bnode, boff, ldir, lq, flags, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_boundary(int precision, const BatchDomain* doms, const int2* items,
+                                  const int* n_items, int grid, cudaStream_t s) {
+  if (precision == LBM_FP32_DEV)
+    batch_boundary_kernel<float><<<grid, 128, 0, s>>>(doms, items, n_items);
+  else if (precision == LBM_FP16_DEV)
+    batch_boundary_kernel<__half><<<grid, 128, 0, s>>>(doms, items, n_items);
+  else
+    batch_boundary_kernel<double><<<grid, 128, 0, s>>>(doms, items, n_items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, cudaStream_t s) {
+  if (n_doms <= 0) return cudaSuccess;
+  batch_advance_kernel<<<(n_doms + 127) / 128, 128, 0, s>>>(doms, n_doms);
   return cudaGetLastError();
 }
 

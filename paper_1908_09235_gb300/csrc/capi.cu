@@ -13,47 +13,8 @@ using namespace lbm;
 namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-constexpr int kDefaultGraphSteps = 32;
 }  // namespace
 
-struct lbm_ctx {
-  DevParams p{};
-  GeomParams g{};
-  int precision = LBM_FP64;
-  size_t lattice_bytes = 0;  // one lattice: 9 planes of nx*ny populations
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  lbm_alloc_fn alloc = nullptr;
-  lbm_free_fn free_fn = nullptr;
-  void* alloc_user = nullptr;
-  std::vector<std::pair<void*, size_t>> blocks;
-  size_t device_bytes = 0;
-  // device buffers
-  void* f[2] = {nullptr, nullptr};
-  int cur = 0;
-  uint8_t* flags = nullptr;
-  double *rho_m = nullptr, *ux_m = nullptr, *uy_m = nullptr;
-  int32_t *bnode = nullptr, *boff = nullptr;
-  uint8_t* ldir = nullptr;
-  double* lq = nullptr;
-  double* carry = nullptr;
-  LinkRecipe recipe{};
-  double* partials = nullptr;
-  double* mass_out = nullptr;
-  int* err_flag = nullptr;
-  int2* geom_tmp = nullptr;
-  long long* geom_totals = nullptr;
-  int ledger_blocks = 0;
-  long long nb = 0, nl = 0, n_fluid = 0;
-  int64_t steps = 0;
-  bool initialized = false;
-  int graph_steps = kDefaultGraphSteps;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  lbm_status status = LBM_OK;
-  std::string msg;
-  double T = 0.0;
-  bool rho_ref_auto = false;  // deviation storage: take rho_ref from the initial state
-};
 
 namespace {
 

@@ -54,7 +54,14 @@ struct Pop<double> {
   static __device__ __forceinline__ void store(void* b, int a, int N, int n, C v) {
     static_cast<double*>(b)[a * N + n] = v;
   }
-  // element e = a N + n
+  // element e = a N + n, in the arithmetic type C; store_t returns the value as stored
+  static __device__ __forceinline__ C load_t(const void* b, int e, int N) {
+    return static_cast<const double*>(b)[e];
+  }
+  static __device__ __forceinline__ C store_t(void* b, int e, int N, C v) {
+    static_cast<double*>(b)[e] = v;
+    return v;
+  }
   static __device__ __forceinline__ double load_e(const void* b, int e, int N) {
     return static_cast<const double*>(b)[e];
   }
@@ -73,6 +80,13 @@ struct Pop<float> {
   static __device__ __forceinline__ C rounded(int a, C v) { return v; }
   static __device__ __forceinline__ void store(void* b, int a, int N, int n, C v) {
     static_cast<float*>(b)[a * N + n] = v;
+  }
+  static __device__ __forceinline__ C load_t(const void* b, int e, int N) {
+    return static_cast<const float*>(b)[e];
+  }
+  static __device__ __forceinline__ C store_t(void* b, int e, int N, C v) {
+    static_cast<float*>(b)[e] = v;
+    return v;
   }
   static __device__ __forceinline__ double load_e(const void* b, int e, int N) {
     return double(static_cast<const float*>(b)[e]);
@@ -104,6 +118,18 @@ struct Pop<__half> {
       static_cast<float*>(b)[n] = v;
     else
       moving(b, N)[(a - 1) * N + n] = __float2half_rn(v);
+  }
+  static __device__ __forceinline__ C load_t(const void* b, int e, int N) {
+    return e < N ? static_cast<const float*>(b)[e] : __half2float(moving(b, N)[e - N]);
+  }
+  static __device__ __forceinline__ C store_t(void* b, int e, int N, C v) {
+    if (e < N) {
+      static_cast<float*>(b)[e] = v;
+      return v;
+    }
+    const __half h = __float2half_rn(v);
+    moving(b, N)[e - N] = h;
+    return __half2float(h);
   }
   static __device__ __forceinline__ double load_e(const void* b, int e, int N) {
     return e < N ? double(static_cast<const float*>(b)[e])

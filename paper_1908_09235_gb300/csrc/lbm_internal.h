@@ -4,6 +4,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/lbm_gb300.h"
 
@@ -63,6 +65,8 @@ struct GeomParams {
   GeomCircle c[kMaxCircles];
 };
 
+struct LinkRecipe;
+
 // ---- launchers (implemented in the .cu files) ----
 // geometry.cu
 cudaError_t launch_geom_solid(const GeomParams& g, uint8_t* flags, cudaStream_t s);
@@ -97,7 +101,31 @@ struct LinkRecipe {
   double* c2;
   double* chi;
   double* cus;
+  float* c0f;     // FP32 copies for the deviation formats
+  float* c1f;
+  float* c2f;
+  float* chif;
+  float* cusf;
 };
+// One lattice of a batch as the batched kernels see it.  cur and steps_left are advanced on
+// the device after every step (batch_advance_kernel), so a captured graph stays valid while
+// lattices join and leave the batch.
+struct BatchDomain {
+  DevParams p;
+  void* f[2];
+  const uint8_t* flags;
+  double *rho_m, *ux_m, *uy_m;
+  const int32_t* bnode;
+  const int32_t* boff;
+  const uint8_t* ldir;
+  LinkRecipe recipe;
+  double* carry;
+  int nb;
+  int cur;
+  long long steps_left;
+  long long steps_done;
+};
+
 size_t link_recipe_bytes(long long nl);
 void link_recipe_carve(char* base, long long nl, LinkRecipe* r);
 cudaError_t launch_link_setup(const DevParams& p, int nb, const int32_t* bnode,
@@ -107,6 +135,16 @@ cudaError_t launch_boundary(int precision, const DevParams& p, int nb, const int
                             const int32_t* boff, const uint8_t* ldir, LinkRecipe r,
                             const void* fa, void* fb, const double* rho_m, const double* ux_m,
                             const double* uy_m, double* carry, cudaStream_t s);
+
+// batched kernels (step.cu, boundary.cu, batch.cu)
+int batch_tile_rows(int ry);
+int batch_tile_cols();
+int batch_step_grid(int precision, int eos, int ry);
+cudaError_t launch_batch_step(int precision, int eos, int ry, const BatchDomain* doms,
+                              const int4* tiles, const int* n_tiles, int grid, cudaStream_t s);
+cudaError_t launch_batch_boundary(int precision, const BatchDomain* doms, const int2* items,
+                                  const int* n_items, int grid, cudaStream_t s);
+cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, cudaStream_t s);
 
 // ledger.cu
 int ledger_num_blocks(int N);
@@ -126,3 +164,43 @@ bool cs_maxwell(double a, double b, double R, double T, double* rho_l, double* r
 double host_psi(const DevParams& p, double rho);
 
 }  // namespace lbm
+
+// State of one lattice (the opaque lbm_ctx of the C ABI).
+struct lbm_ctx {
+  lbm::DevParams p{};
+  lbm::GeomParams g{};
+  int precision = LBM_FP64;
+  size_t lattice_bytes = 0;  // one lattice: 9 planes of nx*ny populations
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  lbm_alloc_fn alloc = nullptr;
+  lbm_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  std::vector<std::pair<void*, size_t>> blocks;
+  size_t device_bytes = 0;
+  // device buffers
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint8_t* flags = nullptr;
+  double *rho_m = nullptr, *ux_m = nullptr, *uy_m = nullptr;
+  int32_t *bnode = nullptr, *boff = nullptr;
+  uint8_t* ldir = nullptr;
+  double* lq = nullptr;
+  double* carry = nullptr;
+  lbm::LinkRecipe recipe{};
+  double* partials = nullptr;
+  double* mass_out = nullptr;
+  int* err_flag = nullptr;
+  int2* geom_tmp = nullptr;
+  long long* geom_totals = nullptr;
+  int ledger_blocks = 0;
+  long long nb = 0, nl = 0, n_fluid = 0;
+  int64_t steps = 0;
+  bool initialized = false;
+  int graph_steps = 32;  // time steps per captured graph
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  lbm_status status = LBM_OK;
+  std::string msg;
+  double T = 0.0;
+  bool rho_ref_auto = false;  // deviation storage: take rho_ref from the initial state
+};

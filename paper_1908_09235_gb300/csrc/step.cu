@@ -38,21 +38,20 @@ __device__ __forceinline__ C pop_sum(const C (&f)[9]) {
   return r;
 }
 
-template <typename S, int EOS, bool FIELDS>
-__global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 : 2)
-    step_kernel(DevParams p, const void* __restrict__ fa, void* __restrict__ fb,
-                                                       const uint8_t* __restrict__ flags,
-                                                       double* __restrict__ rho_m,
-                                                       double* __restrict__ ux_m,
-                                                       double* __restrict__ uy_m) {
+// One tile (x0, y0) of one lattice: every thread of the CTA calls it with the same arguments.
+// psi_s: shared memory of (TYT RY + 2) x (TX + 2) values.
+template <typename S, int EOS, bool FIELDS, int RY>
+__device__ __forceinline__ void step_tile(const DevParams& p, const void* __restrict__ fa,
+                                          void* __restrict__ fb,
+                                          const uint8_t* __restrict__ flags,
+                                          double* __restrict__ rho_m, double* __restrict__ ux_m,
+                                          double* __restrict__ uy_m, int x0, int y0,
+                                          typename Pop<S>::C (*psi_s)[TX + 2]) {
   using C = typename StoreTraits<S>::C;
   constexpr bool DEV = StoreTraits<S>::deviation;
-  constexpr int RY = StoreTraits<S>::RY;
   constexpr int TH = TYT * RY;  // tile height in nodes
-  __shared__ C psi_s[TH + 2][TX + 2];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TH;
   const int nx = p.nx, ny = p.ny;
   const int N = p.N;  // 9 N < 2^31 (checked at creation): 32-bit element offsets
   // ragged tiles of lattices narrower than a tile wrap more than once
@@ -188,10 +187,16 @@ __global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 :
       uy_m[n] = double(uy);
       continue;
     } else {
-      if (fl[r] & FLAG_MACRO) {
-        rho_m[n] = double(rh);
-        ux_m[n] = double(ux);
-        uy_m[n] = double(uy);
+      if (fl[r] & FLAG_MACRO) {  // for the wall pass, in its arithmetic type
+        if constexpr (DEV) {
+          reinterpret_cast<float*>(rho_m)[n] = rh;
+          reinterpret_cast<float*>(ux_m)[n] = ux;
+          reinterpret_cast<float*>(uy_m)[n] = uy;
+        } else {
+          rho_m[n] = rh;
+          ux_m[n] = ux;
+          uy_m[n] = uy;
+        }
       }
       // Collision, Eq. (2): f* = (1 - omega) f + omega f_eq + F_a, with f_eq of Eq. (4),
       //   f_eq = w [c0 + rho eu (3 + 4.5 eu)],  c0 = rho (1 - 1.5 u.u) (less rho_ref if stored
@@ -245,6 +250,40 @@ __global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 :
   }
 }
 
+template <typename S, int EOS, bool FIELDS>
+__global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 : 2)
+    step_kernel(DevParams p, const void* __restrict__ fa, void* __restrict__ fb,
+                const uint8_t* __restrict__ flags, double* __restrict__ rho_m,
+                double* __restrict__ ux_m, double* __restrict__ uy_m) {
+  using C = typename StoreTraits<S>::C;
+  constexpr int RY = StoreTraits<S>::RY;
+  __shared__ C psi_s[TYT * RY + 2][TX + 2];
+  step_tile<S, EOS, FIELDS, RY>(p, fa, fb, flags, rho_m, ux_m, uy_m, blockIdx.x * TX,
+                                blockIdx.y * TYT * RY, psi_s);
+}
+
+// Many lattices in one launch: a persistent grid walks a table of tiles (domain, x0, y0).  Tiles
+// of domains whose step budget is spent are skipped.  RY (rows per thread, so the tile height
+// 8 RY) is the tile shape chosen by the batch's tuner.
+template <typename S, int EOS, int RY>
+__global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 : 2)
+    batch_step_kernel(const BatchDomain* __restrict__ doms, const int4* __restrict__ tiles,
+                      const int* __restrict__ n_tiles) {
+  using C = typename StoreTraits<S>::C;
+  __shared__ C psi_s[TYT * RY + 2][TX + 2];
+  const int nt = *n_tiles;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int4 tile = tiles[t];  // (domain, x0, y0, -)
+    const BatchDomain& D = doms[tile.x];
+    if (D.steps_left <= 0) continue;
+    const int cur = D.cur;
+    step_tile<S, EOS, false, RY>(D.p, D.f[cur], D.f[cur ^ 1], D.flags, D.rho_m, D.ux_m, D.uy_m,
+                                 tile.y, tile.z, psi_s);
+    __syncthreads();  // psi_s is reused by the next tile
+  }
+}
+
+
 template <typename S, int EOS>
 cudaError_t launch_t(const DevParams& p, const void* fa, void* fb, const uint8_t* flags,
                      double* rho_m, double* ux_m, double* uy_m, bool fields_only,
@@ -273,7 +312,69 @@ cudaError_t launch_s(const DevParams& p, const void* fa, void* fb, const uint8_t
   }
 }
 
+template <typename S, int EOS, int RY>
+cudaError_t launch_batch_t(const BatchDomain* doms, const int4* tiles, const int* n_tiles, int grid,
+                           cudaStream_t s) {
+  batch_step_kernel<S, EOS, RY><<<grid, dim3(TX, TYT), 0, s>>>(doms, tiles, n_tiles);
+  return cudaGetLastError();
+}
+
+template <typename S, int RY>
+cudaError_t launch_batch_e(int eos, const BatchDomain* doms, const int4* tiles, const int* n_tiles,
+                           int grid, cudaStream_t s) {
+  switch (eos) {
+    case LBM_EOS_EXP: return launch_batch_t<S, LBM_EOS_EXP, RY>(doms, tiles, n_tiles, grid, s);
+    case LBM_EOS_CS: return launch_batch_t<S, LBM_EOS_CS, RY>(doms, tiles, n_tiles, grid, s);
+    default: return launch_batch_t<S, LBM_EOS_NONE, RY>(doms, tiles, n_tiles, grid, s);
+  }
+}
+
+template <typename S>
+cudaError_t launch_batch_s(int eos, int ry, const BatchDomain* doms, const int4* tiles,
+                           const int* n_tiles, int grid, cudaStream_t s) {
+  if (ry == 1) return launch_batch_e<S, 1>(eos, doms, tiles, n_tiles, grid, s);
+  if (ry == 2) return launch_batch_e<S, 2>(eos, doms, tiles, n_tiles, grid, s);
+  if constexpr (sizeof(typename Pop<S>::C) == 4) {
+    if (ry == 4) return launch_batch_e<S, 4>(eos, doms, tiles, n_tiles, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename S>
+int batch_grid_s(int eos, int ry) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* fn = nullptr;
+  auto pick = [&](auto k) { fn = reinterpret_cast<const void*>(k); };
+  if (ry == 1) pick(batch_step_kernel<S, LBM_EOS_CS, 1>);
+  else if (ry == 2) pick(batch_step_kernel<S, LBM_EOS_CS, 2>);
+  else if constexpr (sizeof(typename Pop<S>::C) == 4) pick(batch_step_kernel<S, LBM_EOS_CS, 4>);
+  if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, TX * TYT, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per = 2;
+  }
+  (void)eos;
+  return sms * (per > 0 ? per : 1);
+}
+
 }  // namespace
+
+int batch_tile_rows(int ry) { return TYT * ry; }
+int batch_tile_cols() { return TX; }
+
+int batch_step_grid(int precision, int eos, int ry) {
+  if (precision == LBM_FP32_DEV) return batch_grid_s<float>(eos, ry);
+  if (precision == LBM_FP16_DEV) return batch_grid_s<__half>(eos, ry);
+  return batch_grid_s<double>(eos, ry);
+}
+
+cudaError_t launch_batch_step(int precision, int eos, int ry, const BatchDomain* doms,
+                              const int4* tiles, const int* n_tiles, int grid, cudaStream_t s) {
+  if (precision == LBM_FP32_DEV) return launch_batch_s<float>(eos, ry, doms, tiles, n_tiles, grid, s);
+  if (precision == LBM_FP16_DEV) return launch_batch_s<__half>(eos, ry, doms, tiles, n_tiles, grid, s);
+  return launch_batch_s<double>(eos, ry, doms, tiles, n_tiles, grid, s);
+}
 
 cudaError_t launch_step(int precision, const DevParams& p, const void* fa, void* fb,
                         const uint8_t* flags, double* rho_m, double* ux_m, double* uy_m,

@@ -29,7 +29,10 @@ STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM
 EXPORTS = ("lbm_create", "lbm_coexistence", "lbm_init_fields", "lbm_init_droplet", "lbm_step",
            "lbm_step_timed", "lbm_mass", "lbm_fields", "lbm_fields_device", "lbm_flags",
            "lbm_links", "lbm_info", "lbm_last_error", "lbm_status_string", "lbm_destroy",
-           "lbm_mass_noalloc")
+           "lbm_mass_noalloc", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
+           "lbm_batch_set_steps", "lbm_batch_step", "lbm_batch_step_timed", "lbm_batch_progress",
+           "lbm_batch_domain", "lbm_batch_tune", "lbm_batch_info", "lbm_domain_bytes",
+           "lbm_batch_last_error", "lbm_batch_destroy")
 
 
 class LBMError(RuntimeError):
@@ -74,6 +77,18 @@ class Info(C.Structure):
                 ("psi_wall", C.c_double)]
 
 
+class Domain(C.Structure):
+    _fields_ = [("geometry", Geometry), ("eos", Eos), ("tau", C.c_double), ("scheme", C.c_int32),
+                ("init", C.c_int32), ("cx", C.c_double), ("cy", C.c_double), ("R", C.c_double),
+                ("W", C.c_double), ("rho_in", C.c_double), ("rho_out", C.c_double)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("active", C.c_int32), ("tiles", C.c_int32), ("tile_rows", C.c_int32),
+                ("tile_cols", C.c_int32), ("nodes", C.c_int64), ("fluid_nodes", C.c_int64),
+                ("boundary_links", C.c_int64), ("device_bytes", C.c_int64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -112,6 +127,21 @@ def load_library(build_if_missing=True):
             "lbm_destroy": (None, [P]),
             "lbm_mass_noalloc": (C.c_int, [V, V, C.c_int32, C.c_int32, C.c_int32, C.c_double, V,
                                            V, V]),
+            "lbm_batch_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(Options),
+                                           C.POINTER(C.c_void_p)]),
+            "lbm_batch_add": (C.c_int, [P, C.POINTER(Domain), C.c_int64, C.POINTER(C.c_int32)]),
+            "lbm_batch_remove": (C.c_int, [P, C.c_int32]),
+            "lbm_batch_set_steps": (C.c_int, [P, C.c_int32, C.c_int64]),
+            "lbm_batch_step": (C.c_int, [P, C.c_int32]),
+            "lbm_batch_step_timed": (C.c_int, [P, C.c_int32, D, D, D]),
+            "lbm_batch_progress": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int64),
+                                             C.POINTER(C.c_int64)]),
+            "lbm_batch_domain": (C.c_int, [P, C.c_int32, C.POINTER(C.c_void_p)]),
+            "lbm_batch_tune": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32)]),
+            "lbm_batch_info": (C.c_int, [P, C.POINTER(BatchInfo)]),
+            "lbm_domain_bytes": (C.c_int, [C.POINTER(Domain), C.c_int32, C.POINTER(C.c_int64)]),
+            "lbm_batch_last_error": (C.c_char_p, [P]),
+            "lbm_batch_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -333,3 +363,128 @@ class Lattice:
 
     def info(self):
         return lbm_info(self.ctx)
+
+
+# ---- batches -------------------------------------------------------------------------------------
+def make_domain(nx, ny, tau, scheme, circles=(), eos=None, droplet=None, rho=1.0, wall_q_lo=0.0,
+                wall_q_hi=0.0):
+    """A lattice description for Batch.add: droplet = (cx, cy, R, W, rho_in, rho_out), else a
+    uniform density rho at rest."""
+    if isinstance(scheme, str):
+        scheme = SCHEMES[scheme]
+    g = make_geometry(nx, ny, circles, wall_q_lo, wall_q_hi)
+    d = Domain()
+    d.geometry = g
+    d.eos = eos if eos is not None else make_eos()
+    d.tau = float(tau)
+    d.scheme = int(scheme)
+    if droplet is not None:
+        d.init = 1
+        d.cx, d.cy, d.R, d.W, d.rho_in, d.rho_out = (float(v) for v in droplet)
+    else:
+        d.init = 0
+        d.rho_in = float(rho)
+    d._keep = g._keep
+    return d
+
+
+def lbm_domain_bytes(domain, precision):
+    n = C.c_int64()
+    _check(None, load_library().lbm_domain_bytes(C.byref(domain), int(precision), C.byref(n)))
+    return n.value
+
+
+class Batch:
+    """Many lattices of one precision and EOS kind advanced together (lbm_batch_* of the C ABI).
+    Device memory comes from PyTorch's allocator unless torch_memory is False."""
+
+    def __init__(self, precision=FP64, eos_kind=EOS_CS, max_domains=64, stream=None,
+                 torch_memory=True):
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        lib = load_library()
+        opt = Options()
+        opt.precision = precision
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        opt.stream = C.c_void_p(int(stream))
+        self.mem = None
+        if torch_memory:
+            self.mem = TorchDeviceMemory()
+            opt.alloc = self.mem.alloc_fn
+            opt.free = self.mem.free_fn
+        self.options = opt
+        self.precision = precision
+        out = C.c_void_p()
+        _check(None, lib.lbm_batch_create(precision, eos_kind, max_domains, C.byref(opt),
+                                          C.byref(out)))
+        self.b = out.value
+        self.shapes = {}
+
+    def _chk(self, st):
+        if st != 0:
+            raise LBMError(st, load_library().lbm_batch_last_error(self.b).decode()
+                           or load_library().lbm_status_string(st).decode())
+
+    def add(self, domain, steps):
+        slot = C.c_int32()
+        self._chk(load_library().lbm_batch_add(self.b, C.byref(domain), int(steps),
+                                               C.byref(slot)))
+        self.shapes[slot.value] = (domain.geometry.nx, domain.geometry.ny)
+        return slot.value
+
+    def remove(self, slot):
+        self._chk(load_library().lbm_batch_remove(self.b, int(slot)))
+        self.shapes.pop(slot, None)
+
+    def set_steps(self, slot, steps):
+        self._chk(load_library().lbm_batch_set_steps(self.b, int(slot), int(steps)))
+
+    def step(self, n):
+        self._chk(load_library().lbm_batch_step(self.b, int(n)))
+
+    def step_timed(self, n):
+        t, a, b = C.c_double(), C.c_double(), C.c_double()
+        self._chk(load_library().lbm_batch_step_timed(self.b, int(n), C.byref(t), C.byref(a),
+                                                      C.byref(b)))
+        return t.value, a.value, b.value
+
+    def progress(self, slot):
+        done, left = C.c_int64(), C.c_int64()
+        self._chk(load_library().lbm_batch_progress(self.b, int(slot), C.byref(done),
+                                                    C.byref(left)))
+        return done.value, left.value
+
+    def ctx(self, slot):
+        c = C.c_void_p()
+        self._chk(load_library().lbm_batch_domain(self.b, int(slot), C.byref(c)))
+        return c.value
+
+    def mass(self, slot):
+        return lbm_mass(self.ctx(slot))
+
+    def fields(self, slot):
+        nx, ny = self.shapes[slot]
+        return lbm_fields(self.ctx(slot), nx, ny)
+
+    def tune(self, trial_steps=5):
+        rows = C.c_int32()
+        self._chk(load_library().lbm_batch_tune(self.b, int(trial_steps), C.byref(rows)))
+        return rows.value
+
+    def info(self):
+        i = BatchInfo()
+        self._chk(load_library().lbm_batch_info(self.b, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def close(self):
+        if getattr(self, "b", None):
+            load_library().lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -48,3 +48,23 @@ LARGE = droplet_on_cylinder(4096, 600.0, 800.0, name="droplet_on_cylinder_4096x4
 # exponential psi with G = -10/3, nu = 0.15 (tau = 0.95), periodic box.
 PAPER_E2 = dict(nx=300, ny=350, cyl=(150.0, 130.0, 70.0), tau=0.95,
                 eos=dict(G=-10.0 / 3.0, psi0=1.0, rho0=1.0), rho_l=2.783, rho_v=0.3675)
+
+
+def batched_domains(n=512, seed=SEED, side_lo=64, side_hi=512):
+    """The batched workload: n independent droplet-on-cylinder lattices with side uniform in
+    {side_lo..side_hi}, cylinder radius 0.15-0.3 x side, droplet radius 0.2-0.35 x side,
+    T/T_c uniform in [0.80, 0.90], tau uniform in [0.6, 1.2] (seeded)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        L = int(rng.integers(side_lo, side_hi + 1))
+        r = float(rng.uniform(0.15, 0.3)) * L
+        R = float(rng.uniform(0.2, 0.35)) * L
+        t = float(rng.uniform(0.80, 0.90))
+        tau = float(rng.uniform(0.6, 1.2))
+        cy = round(0.35 * L)
+        out.append(dict(name="batch_%d" % k, nx=L, ny=L, cyl=(L / 2, cy, r),
+                        drop=(L / 2, cy + r, R, 5.0), tau=tau,
+                        eos=dict(CS, T_over_Tc=t)))
+    return out
