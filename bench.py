@@ -329,6 +329,83 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Served stream of droplet-on-cylinder requests (Poisson arrivals, side log-uniform,
+    steps uniform, scheme from the five variants) through the continuous-batching server with
+    FP32 deviation storage; compared with the plain loop that runs one FP64 lattice at a time."""
+    import numpy as np
+    import torch
+
+    from paper_1908_09235_gb300 import lbm, serve, workloads
+    torch.cuda.set_device(0)
+    reqs = workloads.served_requests(n=args.serve_requests, rate=args.serve_rate,
+                                     steps_lo=args.serve_steps_lo, steps_hi=args.serve_steps_hi)
+    srv = serve.Server(precision=lbm.FP32_DEV, max_slots=args.serve_slots,
+                       hbm_bytes=int(args.serve_hbm_gb * 2**30) if args.serve_hbm_gb else None,
+                       chunk=args.serve_chunk)
+    t0 = time.perf_counter()
+    with Clocks(0) as clk:
+        done = srv.run(reqs)
+    makespan = time.perf_counter() - t0
+    srv.close()
+    work = sum(r.fluid_nodes * r.steps for r in done)
+    value = work / makespan / 1e6
+    stats = serve.latency_stats(done)
+    unstable = sum(1 for r in done if r.result.get("unstable"))
+    # plain loop: one FP64 lattice at a time; per-size FP64 step rate and set-up time measured
+    # here, latencies from a FIFO queue on the same arrivals (a model, not a replay)
+    sizes = [128, 256, 512, 1024]
+    rate, setup = {}, {}
+    for L in sizes:
+        req = dict(workloads.served_requests(n=1, side_lo=L, side_hi=L)[0])
+        t1 = time.perf_counter()
+        eos = lbm.make_eos(lbm.EOS_CS, **req["eos"])
+        rl, rv = lbm.lbm_coexistence(eos)
+        eos.rho_wall = rv
+        lat = lbm.Lattice(L, L, req["tau"], lbm.MOD_B, circles=[req["cyl"]], eos=eos)
+        lat.init_droplet(*req["drop"], rl, rv)
+        lat.mass()
+        setup[L] = time.perf_counter() - t1
+        lat.step_timed(3)
+        _, _, ms = lat.step_timed(20)
+        rate[L] = lat.info()["n_fluid"] * 20 / (ms * 1e-3)
+        lat.fields()
+        lat.close()
+    logs = np.log(sizes)
+
+    def interp(d, L):
+        return float(np.exp(np.interp(np.log(L), logs, np.log([d[s] for s in sizes]))))
+    by_id = {r["rid"]: r for r in reqs}
+    service = [interp(setup, by_id[r.rid]["nx"]) + r.fluid_nodes * r.steps /
+               interp(rate, by_id[r.rid]["nx"]) for r in sorted(done, key=lambda r: r.arrival)]
+    arrivals = [r.arrival for r in sorted(done, key=lambda r: r.arrival)]
+    base_lat = serve.fifo_latencies(arrivals, service)
+    base_makespan = max(a + l for a, l in zip(arrivals, base_lat))
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1,
+            "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served_droplets_%d" % len(reqs), "storage": "fp32_dev",
+                       "arrival_rate_per_s": args.serve_rate, "slots": args.serve_slots,
+                       "chunk_steps": args.serve_chunk,
+                       "hbm_budget_bytes": srv.hbm_bytes},
+            "served": {"requests": len(done), "makespan_s": round(makespan, 2),
+                       "p50_latency_s": round(stats["p50_s"], 3),
+                       "p99_latency_s": round(stats["p99_s"], 3),
+                       "max_concurrent": srv.max_concurrent,
+                       "peak_admitted_bytes": srv.peak_bytes, "unstable_results": unstable,
+                       "node_steps": work},
+            "plain_fp64_loop_model": {
+                "mlups": round(work / base_makespan / 1e6, 1),
+                "makespan_s": round(base_makespan, 1),
+                "p50_latency_s": round(float(np.percentile(base_lat, 50)), 2),
+                "p99_latency_s": round(float(np.percentile(base_lat, 99)), 2),
+                "fp64_fluid_mlups_by_side": {str(k): round(v / 1e6, 1) for k, v in rate.items()},
+                "how": "FIFO queue on the same arrivals with service time = measured FP64 "
+                       "set-up + fluid nodes x steps / measured FP64 step rate of that size"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,6 +421,16 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="the batched workload: many uneven lattices in one batch")
     ap.add_argument("--batch-domains", type=int, default=512)
+    ap.add_argument("--serve", action="store_true",
+                    help="the served stream through the continuous-batching server")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-steps-lo", type=int, default=2000)
+    ap.add_argument("--serve-steps-hi", type=int, default=20000)
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--serve-chunk", type=int, default=200)
+    ap.add_argument("--serve-hbm-gb", type=float, default=0.0,
+                    help="memory budget of the server (0: 80% of the free device memory)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -355,6 +442,8 @@ def main():
         return run_profile_case(args)
     if args.batched:
         return run_batched(args)
+    if args.serve:
+        return run_serve(args)
 
     import torch
     world, rank, local = dist_setup()

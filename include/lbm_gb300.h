@@ -254,6 +254,8 @@ lbm_status lbm_batch_step_timed(lbm_batch* b, int32_t n, double* ms_total, doubl
 /* Steps done and left of a lattice (blocks). */
 lbm_status lbm_batch_progress(lbm_batch* b, int32_t slot, int64_t* steps_done,
                               int64_t* steps_left);
+/* Steps left of slots 0..n-1 in one call (-1 for an empty slot); blocks. */
+lbm_status lbm_batch_poll(lbm_batch* b, int32_t n, int64_t* steps_left);
 /* The lattice's context, current as of this call, for lbm_mass, lbm_fields, lbm_info (blocks).
  * It stays owned by the batch; do not step or destroy it directly. */
 lbm_status lbm_batch_domain(lbm_batch* b, int32_t slot, lbm_ctx** ctx);

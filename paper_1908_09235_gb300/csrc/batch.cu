@@ -387,6 +387,16 @@ lbm_status lbm_batch_progress(lbm_batch* b, int32_t slot, int64_t* steps_done,
   return LBM_OK;
 }
 
+lbm_status lbm_batch_poll(lbm_batch* b, int32_t n, int64_t* steps_left) {
+  if (!b || n < 0 || (n > 0 && !steps_left)) return LBM_EINVAL;
+  if (b->status) return b->status;
+  lbm_status st = sync_down(b);
+  if (st != LBM_OK) return st;
+  for (int d = 0; d < n; ++d)
+    steps_left[d] = (d < b->max_domains && b->slots[d]) ? b->h_doms[d].steps_left : -1;
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_domain(lbm_batch* b, int32_t slot, lbm_ctx** ctx) {
   if (!valid_slot(b, slot) || !ctx) return LBM_EINVAL;
   if (b->status) return b->status;

@@ -32,7 +32,7 @@ EXPORTS = ("lbm_create", "lbm_coexistence", "lbm_init_fields", "lbm_init_droplet
            "lbm_mass_noalloc", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
            "lbm_batch_set_steps", "lbm_batch_step", "lbm_batch_step_timed", "lbm_batch_progress",
            "lbm_batch_domain", "lbm_batch_tune", "lbm_batch_info", "lbm_domain_bytes",
-           "lbm_batch_last_error", "lbm_batch_destroy")
+           "lbm_batch_last_error", "lbm_batch_destroy", "lbm_batch_poll")
 
 
 class LBMError(RuntimeError):
@@ -142,6 +142,7 @@ def load_library(build_if_missing=True):
             "lbm_domain_bytes": (C.c_int, [C.POINTER(Domain), C.c_int32, C.POINTER(C.c_int64)]),
             "lbm_batch_last_error": (C.c_char_p, [P]),
             "lbm_batch_destroy": (None, [P]),
+            "lbm_batch_poll": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -455,6 +456,12 @@ class Batch:
         self._chk(load_library().lbm_batch_progress(self.b, int(slot), C.byref(done),
                                                     C.byref(left)))
         return done.value, left.value
+
+    def poll(self, n):
+        """steps left of slots 0..n-1 (-1: empty), one synchronisation"""
+        arr = (C.c_int64 * max(1, n))()
+        self._chk(load_library().lbm_batch_poll(self.b, int(n), arr))
+        return list(arr)[:n]
 
     def ctx(self, slot):
         c = C.c_void_p()

@@ -68,3 +68,28 @@ def batched_domains(n=512, seed=SEED, side_lo=64, side_hi=512):
                         drop=(L / 2, cy + r, R, 5.0), tau=tau,
                         eos=dict(CS, T_over_Tc=t)))
     return out
+
+
+SERVED_SCHEMES = ("mls", "bouzidi_l", "zhao_yong", "mod_a", "mod_b")
+
+
+def served_requests(n=2000, rate=200.0, seed=SEED, side_lo=128, side_hi=1024, steps_lo=2000,
+                    steps_hi=20000, schemes=SERVED_SCHEMES):
+    """The served stream: n droplet-on-cylinder requests with Poisson arrivals (mean `rate` per
+    second), lattice side log-uniform in [side_lo, side_hi], steps uniform in [steps_lo,
+    steps_hi], boundary scheme drawn from `schemes`; geometry and fluid as the 4096^2 lattice,
+    scaled (cylinder 0.15 L, droplet 0.2 L)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    out = []
+    for k in range(n):
+        L = int(round(np.exp(rng.uniform(np.log(side_lo), np.log(side_hi)))))
+        steps = int(rng.integers(steps_lo, steps_hi + 1))
+        scheme = schemes[int(rng.integers(len(schemes)))]
+        cy = round(0.35 * L)
+        r = 0.15 * L
+        out.append(dict(rid=k, arrival=float(t[k]), nx=L, ny=L, steps=steps, scheme=scheme,
+                        cyl=(L / 2, cy, r), drop=(L / 2, cy + r, 0.2 * L, 5.0), tau=1.0,
+                        eos=dict(CS)))
+    return out
