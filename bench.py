@@ -150,13 +150,13 @@ def barrier(world):
         dist.barrier()
 
 
-def make_lattice(w, scheme, precision):
+def make_lattice(w, scheme, precision, kernel_path=0):
     from paper_1908_09235_gb300 import lbm
     eos = lbm.make_eos(lbm.EOS_CS, **w.eos)
     rl, rv = lbm.lbm_coexistence(eos)
     eos.rho_wall = rv
     lat = lbm.Lattice(w.nx, w.ny, w.tau, scheme, circles=w.circles, eos=eos,
-                      precision=precision)
+                      precision=precision, kernel_path=kernel_path)
     lat.init_droplet(*w.drop, rl, rv)
     return lat, (rl, rv)
 
@@ -245,13 +245,15 @@ def run_profile_case(args):
     from paper_1908_09235_gb300 import lbm, workloads
     L = args.profile_case
     w = workloads.droplet_on_cylinder(L, 0.15 * L, 0.2 * L)
-    lat, _ = make_lattice(w, lbm.SCHEMES[args.scheme], lbm.PRECISIONS[args.precision])
+    lat, _ = make_lattice(w, lbm.SCHEMES[args.scheme], lbm.PRECISIONS[args.precision],
+                          args.kernel_path)
     lat.step_timed(args.warmup)
     ms = lat.step_timed(args.steps)
     torch.cuda.synchronize()
     info = lat.info()
     lat.close()
     print(json.dumps({"profile_case": w.name, "precision": args.precision, "scheme": args.scheme,
+                      "kernel_path": args.kernel_path,
                       "steps": args.steps, "step_kernel_us": 1e3 * ms[0] / args.steps,
                       "boundary_kernel_us": 1e3 * ms[1] / args.steps,
                       "fluid_nodes": info["n_fluid"]}), flush=True)
@@ -418,6 +420,8 @@ def main():
                     help="only run a droplet-on-cylinder lattice of this side (for ncu)")
     ap.add_argument("--precision", default="fp32_dev", choices=["fp64", "fp32_dev", "fp16_dev"])
     ap.add_argument("--scheme", default="mod_b")
+    ap.add_argument("--kernel-path", type=int, default=0,
+                    help="profile case only: 0 tile kernel, 2 TMA-staged tiles")
     ap.add_argument("--batched", action="store_true",
                     help="the batched workload: many uneven lattices in one batch")
     ap.add_argument("--batch-domains", type=int, default=512)

@@ -120,6 +120,10 @@ typedef struct {
   void* alloc_user;
   double rho_ref;      /* reference density of the deviation formats; <= 0: the smallest       *
                         * initial fluid density, set by lbm_init_fields / lbm_init_droplet      */
+  int32_t kernel_path; /* 0 or 1: tile kernel with per-thread loads (the faster one measured);  *
+                        * 2: FP32 deviations on lattices with nx % 16 == 0, nx, ny >= 64: a     *
+                        * persistent kernel that stages tiles by TMA (same results, bit for bit) */
+  int32_t pad;
 } lbm_options;
 
 typedef struct {

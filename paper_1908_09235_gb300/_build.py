@@ -13,8 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["step.cu", "boundary.cu", "geometry.cu", "ledger.cu", "capi.cu", "batch.cu",
-                "mass_noalloc.cu"]
+CUDA_SOURCES = ["step.cu", "step_tma.cu", "boundary.cu", "geometry.cu", "ledger.cu", "capi.cu",
+                "batch.cu", "mass_noalloc.cu"]
 CXX_SOURCES = ["eos_host.cpp"]
 
 
@@ -26,7 +26,7 @@ def _nvcc():
 
 
 def _sources():
-    names = CUDA_SOURCES + CXX_SOURCES + ["d2q9.cuh", "lbm_internal.h"]
+    names = CUDA_SOURCES + CXX_SOURCES + ["d2q9.cuh", "step_core.cuh", "lbm_internal.h"]
     paths = [os.path.join(CSRC, n) for n in names]
     paths.append(os.path.join(os.path.dirname(HERE), "include", "lbm_gb300.h"))
     paths.append(os.path.abspath(__file__))

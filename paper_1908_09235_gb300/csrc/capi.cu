@@ -79,11 +79,18 @@ struct Carver {
   }
 };
 
+cudaError_t launch_bulk(lbm_ctx* c, cudaStream_t s, int cur) {
+  if (c->use_tma)
+    return launch_step_tma(c->tmap[cur], c->fmap, c->p, c->f[cur], c->f[1 - cur], c->flags,
+                           c->rho_m, c->ux_m, c->uy_m, c->err_flag, s);
+  return launch_step(c->precision, c->p, c->f[cur], c->f[1 - cur], c->flags, c->rho_m, c->ux_m,
+                     c->uy_m, false, s);
+}
+
 lbm_status launch_one_step(lbm_ctx* c, cudaStream_t s, int cur) {
   const void* fa = c->f[cur];
   void* fb = c->f[1 - cur];
-  cudaError_t e = launch_step(c->precision, c->p, fa, fb, c->flags, c->rho_m, c->ux_m, c->uy_m,
-                              false, s);
+  cudaError_t e = launch_bulk(c, s, cur);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
   e = launch_boundary(c->precision, c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->recipe, fa,
                       fb, c->rho_m, c->ux_m, c->uy_m, c->carry, s);
@@ -338,6 +345,10 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
     return bail(e, "memset f0");
   if ((e = cudaMemsetAsync(c->f[1], 0, c->lattice_bytes, c->stream)) != cudaSuccess)
     return bail(e, "memset f1");
+  if (opt && opt->kernel_path == 2 && tma_step_supported(precision, geo->nx, geo->ny))
+    c->use_tma = make_lattice_tensor_map(c->tmap[0], c->f[0], geo->nx, geo->ny) &&
+                 make_lattice_tensor_map(c->tmap[1], c->f[1], geo->nx, geo->ny) &&
+                 make_flags_tensor_map(c->fmap, c->flags, geo->nx, geo->ny);
   *out = c;
   return LBM_OK;
 }
@@ -439,8 +450,7 @@ lbm_status lbm_step_timed(lbm_ctx* c, int32_t n, double* ms_step, double* ms_bnd
   LBM_CUDA(c, cudaEventRecord(ev[0], c->stream));
   for (int k = 0; k < n && st == LBM_OK; ++k) {
     const int cur = c->cur;
-    cudaError_t e = launch_step(c->precision, c->p, c->f[cur], c->f[1 - cur], c->flags, c->rho_m,
-                                c->ux_m, c->uy_m, false, c->stream);
+    cudaError_t e = launch_bulk(c, c->stream, cur);
     if (e != cudaSuccess) st = cuda_fail(c, e, "step kernel launch");
     if (st == LBM_OK) cudaEventRecord(ev[2 * k + 1], c->stream);
     if (st == LBM_OK) {
@@ -488,6 +498,7 @@ lbm_status lbm_mass(lbm_ctx* c, double* out) {
   LBM_CUDA(c, cudaMemcpyAsync(&err, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   *out = m;
+  if (err & kErrTimeout) return fail(c, LBM_ETIMEOUT, "a bounded wait for a tile copy expired");
   if (err) return fail(c, LBM_EUNSTABLE, "non-positive or non-finite density in the fluid");
   return LBM_OK;
 }

@@ -149,16 +149,28 @@ struct Pop<__half> {
 
 // psi(rho): exponential psi0 exp(-rho0/rho) (Sec. 3.2) or the Carnahan-Starling form
 // sqrt(2 (p - rho/3)/G); zero for a single-phase fluid.
+// Division, reciprocal, square root and exponential in the arithmetic type: correctly rounded
+// in FP64; in FP32 the hardware approximations (relative error of a few 2^-24, well inside the
+// FP32 error budget of the method's steady state) to keep the FP32 step memory-bound.
+__device__ __forceinline__ double q_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float q_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double q_rcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float q_rcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double q_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float q_sqrt(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
+__device__ __forceinline__ double q_exp(double a) { return exp(a); }
+__device__ __forceinline__ float q_exp(float a) { return __expf(a); }
+
 template <typename C, int EOS>
 __device__ __forceinline__ C psi_of(const Consts<C>& k, C rho) {
   if constexpr (EOS == LBM_EOS_EXP) {
-    return k.psi0 * exp(-k.rho0 / rho);
+    return k.psi0 * q_exp(-q_div(k.rho0, rho));
   } else if constexpr (EOS == LBM_EOS_CS) {
     const C eta = k.b4 * rho;
     const C om = C(1) - eta;
     const C num = C(1) + eta + eta * eta - eta * eta * eta;
-    const C pr = rho * k.RT * num / (om * om * om) - k.a * rho * rho;
-    return sqrt((pr - rho * C(1.0 / 3.0)) * k.two_over_G);
+    const C pr = q_div(rho * k.RT * num, om * om * om) - k.a * rho * rho;
+    return q_sqrt((pr - rho * C(1.0 / 3.0)) * k.two_over_G);
   } else {
     return C(0);
   }

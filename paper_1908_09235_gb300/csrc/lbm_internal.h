@@ -158,6 +158,16 @@ cudaError_t launch_droplet_rho(const DevParams& p, double cx, double cy, double 
                                double rho_in, double rho_out, double* rho, double* ux, double* uy,
                                cudaStream_t s);
 
+// step_tma.cu
+bool tma_step_supported(int precision, int nx, int ny);
+bool make_lattice_tensor_map(void* map, const void* base, int nx, int ny);
+bool make_flags_tensor_map(void* map, const void* base, int nx, int ny);
+cudaError_t launch_step_tma(const void* map, const void* flag_map, const DevParams& p,
+                            const void* fa, void* fb, const uint8_t* flags, double* rho_m,
+                            double* ux_m, double* uy_m, int* err, cudaStream_t s);
+constexpr int kErrUnstable = 1;  // bits of the context's device error word
+constexpr int kErrTimeout = 4;
+
 // eos_host.cpp
 bool cs_critical_point(double a, double b, double R, double* Tc, double* rhoc);
 bool cs_maxwell(double a, double b, double R, double T, double* rho_l, double* rho_v);
@@ -203,4 +213,7 @@ struct lbm_ctx {
   std::string msg;
   double T = 0.0;
   bool rho_ref_auto = false;  // deviation storage: take rho_ref from the initial state
+  bool use_tma = false;       // step kernel with TMA halo staging (step_tma.cu)
+  alignas(64) unsigned char tmap[2][128];  // tensor maps of the two lattices
+  alignas(64) unsigned char fmap[128];     // tensor map of the node flags
 };

@@ -1,0 +1,346 @@
+// Fused step with TMA halo staging (FP32 deviation storage): the same per-node arithmetic as
+// step_kernel (csrc/step_core.cuh), but a persistent CTA of 512 threads (two CTAs per SM) stages
+// each 32 x 32 tile together with
+// its one-node ring, in all nine planes, into shared memory with a single tensor copy
+// (cp.async.bulk.tensor.3d, box 40 x 34 x 9 starting at (x0 - 4, y0 - 1): the x start stays
+// 16-byte aligned), double-buffered on mbarriers so the copy of the CTA's next tile runs while
+// the current one is computed.  Tiles that touch the periodic seam (whose ring wraps) are staged
+// with plain loads instead.  Every mbarrier wait is bounded (about 2 s): on expiry the CTA
+// records an error (kErrTimeout in the context's error word, reported as LBM_ETIMEOUT by
+// lbm_mass), waits boundedly for its own copies in flight and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "step_core.cuh"
+
+namespace lbm {
+
+namespace {
+
+using namespace step_core;
+
+constexpr int TYM = 16;                   // threads of a CTA in y (512 threads)
+constexpr int RYT = 2;                    // rows per thread: tile 32 x 32
+constexpr int TH = TYM * RYT;             // 32
+constexpr int NT = TX * TYM;              // threads per CTA
+constexpr int SW = TX + 8;                // staged width: x0 - 4 .. x0 + 35
+constexpr int SH = TH + 2;                // staged height: y0 - 1 .. y0 + 32
+constexpr int PLANE = SH * SW;            // floats per plane of a stage
+constexpr int STAGE_FLOATS = 9 * PLANE;   // 12240 floats
+constexpr uint32_t POP_BYTES = STAGE_FLOATS * 4;   // 48960 bytes of populations per tile
+constexpr int FW = 64;                             // staged flag width: x0 - 16 .. x0 + 47
+constexpr uint32_t FLAG_BYTES = FW * SH;           // 2176 bytes of node flags per tile
+constexpr uint32_t FLAG_OFF = (POP_BYTES + 127) / 128 * 128;
+constexpr uint32_t STAGE_BYTES = POP_BYTES + FLAG_BYTES;  // bytes the copies bring per tile
+constexpr uint32_t STAGE_STRIDE = (FLAG_OFF + FLAG_BYTES + 127) / 128 * 128;
+constexpr int NSTAGE = 2;
+constexpr size_t SMEM_BYTES = NSTAGE * STAGE_STRIDE + (TH + 2) * (TX + 2) * 4;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of one mbarrier wait
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the given phase of a stage's barrier; false after about kWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (long long i = 0; i < (1LL << 32); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// A tile whose staged boxes lie inside the lattice (no periodic wrap): copied by TMA.
+__device__ __forceinline__ bool tma_tile(int x0, int y0, int nx, int ny) {
+  return x0 >= 32 && x0 + 48 <= nx && y0 >= 1 && y0 + 33 <= ny;
+}
+
+template <int EOS>
+__global__ void __launch_bounds__(TX* TYM, 2)
+    step_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+                    const __grid_constant__ CUtensorMap fmap, DevParams p,
+                    const float* __restrict__ fa, void* __restrict__ fb,
+                    const uint8_t* __restrict__ flags, double* __restrict__ rho_m,
+                    double* __restrict__ ux_m, double* __restrict__ uy_m, int tiles_x,
+                    int n_tiles, int* __restrict__ err) {
+  using C = float;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* stage[NSTAGE] = {reinterpret_cast<float*>(smem_raw),
+                          reinterpret_cast<float*>(smem_raw + STAGE_STRIDE)};
+  C(*psi_s)[TX + 2] = reinterpret_cast<C(*)[TX + 2]>(smem_raw + NSTAGE * STAGE_STRIDE);
+  __shared__ __align__(8) uint64_t bars[NSTAGE];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int nx = p.nx, ny = p.ny, N = p.N;
+  const Consts<C>& k = p.k<C>();
+  const C rho_ref = k.rho_ref, psi_w = k.psi_wall;
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto tile_xy = [&](int t, int& x0, int& y0) {
+    x0 = (t % tiles_x) * TX;
+    y0 = (t / tiles_x) * TH;
+  };
+  auto issue = [&](int t, int s) {  // by thread 0
+    int x0, y0;
+    tile_xy(t, x0, y0);
+    fence_proxy_async();  // generic reads of this stage precede the async-proxy writes
+    mbar_expect_tx(&bars[s], STAGE_BYTES);
+    tma_load_3d(stage[s], &tmap, &bars[s], x0 - 4, y0 - 1, 0);
+    tma_load_2d(reinterpret_cast<unsigned char*>(stage[s]) + FLAG_OFF, &fmap, &bars[s], x0 - 16,
+                y0 - 1);
+  };
+
+  uint32_t phase = 0;     // bit s: parity of the next completion of stage s
+  uint32_t inflight = 0;  // bit s: a copy into stage s has been issued and not waited for
+  int t = blockIdx.x;
+  if (t < n_tiles) {
+    int x0, y0;
+    tile_xy(t, x0, y0);
+    if (tma_tile(x0, y0, nx, ny)) {
+      if (tid == 0) issue(t, 0);
+      inflight |= 1u;
+    }
+  }
+  for (int it = 0; t < n_tiles; ++it, t += gridDim.x) {
+    const int s = it & 1;
+    int x0, y0;
+    tile_xy(t, x0, y0);
+    // prefetch the next tile of this CTA into the other stage (freed at the end of the last
+    // iteration)
+    const int tn = t + gridDim.x;
+    if (tn < n_tiles) {
+      int xn, yn;
+      tile_xy(tn, xn, yn);
+      if (tma_tile(xn, yn, nx, ny)) {
+        if (tid == 0) issue(tn, s ^ 1);
+        inflight |= 1u << (s ^ 1);
+      }
+    }
+    float* st = stage[s];
+    uint8_t* sfl = reinterpret_cast<uint8_t*>(st) + FLAG_OFF;  // [SH][FW], column 16 is x0
+    if (inflight & (1u << s)) {
+      const bool ok = mbar_wait_bounded(&bars[s], (phase >> s) & 1u);
+      phase ^= 1u << s;
+      inflight &= ~(1u << s);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(err, kErrTimeout);
+        for (int q = 0; q < NSTAGE; ++q)  // bounded drain of this CTA's copies in flight
+          if (inflight & (1u << q)) mbar_wait_bounded(&bars[q], (phase >> q) & 1u);
+        return;
+      }
+    } else {
+      // staged by plain loads with periodic wrap
+      for (int e = tid; e < STAGE_FLOATS; e += NT) {
+        const int a = e / PLANE, rem = e - a * PLANE;
+        const int row = rem / SW, col = rem - row * SW;
+        const int gx = wrap_any(x0 - 4 + col, nx), gy = wrap_any(y0 - 1 + row, ny);
+        st[e] = fa[a * N + gy * nx + gx];
+      }
+      for (int e = tid; e < (int)FLAG_BYTES; e += NT) {
+        const int row = e / FW, col = e - row * FW;
+        const int gx = wrap_any(x0 - 16 + col, nx), gy = wrap_any(y0 - 1 + row, ny);
+        sfl[e] = flags[gy * nx + gx];
+      }
+      __syncthreads();
+    }
+
+    // phase 1 from the stage: own nodes and the ring (lattices of at least 64 x 64: one wrap)
+    C f[RYT][9];
+    C rho[RYT];
+    uint8_t fl[RYT];
+#pragma unroll
+    for (int r = 0; r < RYT; ++r) {
+      const int row = ty + r * TYM + 1;
+      fl[r] = sfl[row * FW + tx + 16];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) f[r][a] = st[a * PLANE + row * SW + tx + 4];
+      rho[r] = (fl[r] & FLAG_SOLID) ? C(1) : rho_ref + pop_sum<C>(f[r]);
+      if constexpr (EOS != LBM_EOS_NONE)
+        psi_s[row][tx + 1] = (fl[r] & FLAG_SOLID) ? psi_w : psi_of<C, EOS>(k, rho[r]);
+    }
+    if constexpr (EOS != LBM_EOS_NONE) {
+      constexpr int kRing = 2 * (TX + 2) + 2 * TH;
+      if (tid < kRing) {
+        const int c = tid;
+        int hx, hy;
+        if (c < 2 * (TX + 2)) {
+          hx = c < TX + 2 ? c : c - (TX + 2);
+          hy = c < TX + 2 ? 0 : TH + 1;
+        } else {
+          const int kk = c - 2 * (TX + 2);
+          hx = kk < TH ? 0 : TX + 1;
+          hy = (kk < TH ? kk : kk - TH) + 1;
+        }
+        C ps = psi_w;
+        if (!(sfl[hy * FW + hx + 15] & FLAG_SOLID)) {
+          C v[9];
+#pragma unroll
+          for (int a = 0; a < 9; ++a) v[a] = st[a * PLANE + hy * SW + hx + 3];
+          ps = psi_of<C, EOS>(k, rho_ref + pop_sum<C>(v));
+        }
+        psi_s[hy][hx] = ps;
+      }
+    }
+    __syncthreads();
+    tile_phase2<float, EOS, false, RYT, TYM>(p, fb, rho_m, ux_m, uy_m, x0, y0, psi_s, f, rho,
+                                             fl);
+    __syncthreads();  // the stage and psi_s are free for the next tile
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+template <int EOS>
+cudaError_t launch_tma_t(const CUtensorMap& map, const CUtensorMap& fmap, const DevParams& p,
+                         const void* fa, void* fb,
+                         const uint8_t* flags, double* rho_m, double* ux_m, double* uy_m,
+                         int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<EOS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles_x = (p.nx + TX - 1) / TX, tiles_y = (p.ny + TH - 1) / TH;
+  const int n_tiles = tiles_x * tiles_y;
+  int grid = 2 * sms;
+  if (grid > n_tiles) grid = n_tiles;
+  step_tma_kernel<EOS><<<grid, dim3(TX, TYM), SMEM_BYTES, s>>>(
+      map, fmap, p, static_cast<const float*>(fa), fb, flags, rho_m, ux_m, uy_m, tiles_x, n_tiles, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tma_step_supported(int precision, int nx, int ny) {
+  return precision == LBM_FP32_DEV && nx % 16 == 0 && nx >= 64 && ny >= 64 &&
+         encoder() != nullptr;
+}
+
+// Tensor map of the node flags: dims (nx, ny) bytes, box 64 x 34.
+bool make_flags_tensor_map(void* map, const void* base, int nx, int ny) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)nx};
+  const cuuint32_t box[2] = {FW, SH};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                  const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Tensor map of one FP32 lattice: dims (nx, ny, 9), box 40 x 34 x 9.
+bool make_lattice_tensor_map(void* map, const void* base, int nx, int ny) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t box[3] = {SW, SH, 9};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                  const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_step_tma(const void* map, const void* flag_map, const DevParams& p,
+                            const void* fa, void* fb, const uint8_t* flags, double* rho_m,
+                            double* ux_m, double* uy_m, int* err, cudaStream_t s) {
+  const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
+  const CUtensorMap& fm = *static_cast<const CUtensorMap*>(flag_map);
+  switch (p.eos) {
+    case LBM_EOS_EXP:
+      return launch_tma_t<LBM_EOS_EXP>(m, fm, p, fa, fb, flags, rho_m, ux_m, uy_m, err, s);
+    case LBM_EOS_CS:
+      return launch_tma_t<LBM_EOS_CS>(m, fm, p, fa, fb, flags, rho_m, ux_m, uy_m, err, s);
+    default:
+      return launch_tma_t<LBM_EOS_NONE>(m, fm, p, fa, fb, flags, rho_m, ux_m, uy_m, err, s);
+  }
+}
+
+}  // namespace lbm
