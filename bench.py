@@ -421,7 +421,7 @@ def main():
     ap.add_argument("--precision", default="fp32_dev", choices=["fp64", "fp32_dev", "fp16_dev"])
     ap.add_argument("--scheme", default="mod_b")
     ap.add_argument("--kernel-path", type=int, default=0,
-                    help="profile case only: 0 tile kernel, 2 TMA-staged tiles")
+                    help="profile case only: 0 fastest, 1 scalar tiles, 2 TMA-staged tiles, 3 vectorised")
     ap.add_argument("--batched", action="store_true",
                     help="the batched workload: many uneven lattices in one batch")
     ap.add_argument("--batch-domains", type=int, default=512)

@@ -120,9 +120,15 @@ typedef struct {
   void* alloc_user;
   double rho_ref;      /* reference density of the deviation formats; <= 0: the smallest       *
                         * initial fluid density, set by lbm_init_fields / lbm_init_droplet      */
-  int32_t kernel_path; /* 0 or 1: tile kernel with per-thread loads (the faster one measured);  *
+  int32_t kernel_path; /* step kernel, all with the same results bit for bit:                  *
+                        * 0: the fastest measured: for FP32/FP16 deviations with nx % 4 == 0    *
+                        *    and ny >= 8 the vectorised kernel (population vectors of 16 B,     *
+                        *    halo staged by cp.async), otherwise the scalar tile kernel;         *
+                        * 1: the scalar tile kernel (one node per thread and row);              *
                         * 2: FP32 deviations on lattices with nx % 16 == 0, nx, ny >= 64: a     *
-                        * persistent kernel that stages tiles by TMA (same results, bit for bit) */
+                        *    persistent kernel that stages tiles by TMA; otherwise as 0;         *
+                        * 3: the vectorised kernel wherever nx % 4 == 0 (FP64: nx % 2 == 0) and *
+                        *    ny >= 8, FP64 included; otherwise the scalar tile kernel            */
   int32_t pad;
 } lbm_options;
 

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["step.cu", "step_tma.cu", "boundary.cu", "geometry.cu", "ledger.cu", "capi.cu",
+CUDA_SOURCES = ["step.cu", "step_vec.cu", "step_tma.cu", "boundary.cu", "geometry.cu", "ledger.cu", "capi.cu",
                 "batch.cu", "mass_noalloc.cu"]
 CXX_SOURCES = ["eos_host.cpp"]
 

@@ -84,7 +84,7 @@ cudaError_t launch_bulk(lbm_ctx* c, cudaStream_t s, int cur) {
     return launch_step_tma(c->tmap[cur], c->fmap, c->p, c->f[cur], c->f[1 - cur], c->flags,
                            c->rho_m, c->ux_m, c->uy_m, c->err_flag, s);
   return launch_step(c->precision, c->p, c->f[cur], c->f[1 - cur], c->flags, c->rho_m, c->ux_m,
-                     c->uy_m, false, s);
+                     c->uy_m, false, s, c->kernel_path);
 }
 
 lbm_status launch_one_step(lbm_ctx* c, cudaStream_t s, int cur) {
@@ -345,6 +345,7 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
     return bail(e, "memset f0");
   if ((e = cudaMemsetAsync(c->f[1], 0, c->lattice_bytes, c->stream)) != cudaSuccess)
     return bail(e, "memset f1");
+  c->kernel_path = opt ? opt->kernel_path : 0;
   if (opt && opt->kernel_path == 2 && tma_step_supported(precision, geo->nx, geo->ny))
     c->use_tma = make_lattice_tensor_map(c->tmap[0], c->f[0], geo->nx, geo->ny) &&
                  make_lattice_tensor_map(c->tmap[1], c->f[1], geo->nx, geo->ny) &&
@@ -508,7 +509,7 @@ lbm_status lbm_fields_device(lbm_ctx* c, double* rho, double* ux, double* uy) {
   if (c->status) return c->status;
   if (!c->initialized) return fail(c, LBM_ESTATE, "lbm_fields before initialisation");
   LBM_CUDA(c, launch_step(c->precision, c->p, c->f[c->cur], nullptr, c->flags, rho, ux, uy, true,
-                          c->stream));
+                          c->stream, c->kernel_path));
   return LBM_OK;
 }
 

@@ -161,16 +161,31 @@ __device__ __forceinline__ float q_sqrt(float a) { return a > 0.f ? a * rsqrtf(a
 __device__ __forceinline__ double q_exp(double a) { return exp(a); }
 __device__ __forceinline__ float q_exp(float a) { return __expf(a); }
 
+// Explicitly rounded arithmetic (no contraction freedom for the compiler): every kernel that
+// inlines the per-node arithmetic (the scalar and the vectorised tile cores, the batched kernel)
+// then produces the same bits for the same node.
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename C, int EOS>
 __device__ __forceinline__ C psi_of(const Consts<C>& k, C rho) {
   if constexpr (EOS == LBM_EOS_EXP) {
-    return k.psi0 * q_exp(-q_div(k.rho0, rho));
+    return r_mul(k.psi0, q_exp(-q_div(k.rho0, rho)));
   } else if constexpr (EOS == LBM_EOS_CS) {
-    const C eta = k.b4 * rho;
-    const C om = C(1) - eta;
-    const C num = C(1) + eta + eta * eta - eta * eta * eta;
-    const C pr = q_div(rho * k.RT * num, om * om * om) - k.a * rho * rho;
-    return q_sqrt((pr - rho * C(1.0 / 3.0)) * k.two_over_G);
+    // p = rho R T (1 + eta + eta^2 - eta^3) / (1 - eta)^3 - a rho^2,  eta = b rho / 4
+    const C eta = r_mul(k.b4, rho);
+    const C om = r_sub(C(1), eta);
+    const C e2 = r_mul(eta, eta);
+    const C num = r_sub(r_add(r_add(C(1), eta), e2), r_mul(e2, eta));
+    const C om3 = r_mul(r_mul(om, om), om);
+    const C pr = r_sub(q_div(r_mul(r_mul(rho, k.RT), num), om3), r_mul(r_mul(k.a, rho), rho));
+    return q_sqrt(r_mul(r_sub(pr, r_mul(rho, C(1.0 / 3.0))), k.two_over_G));
   } else {
     return C(0);
   }

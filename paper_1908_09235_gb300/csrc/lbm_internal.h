@@ -80,9 +80,19 @@ cudaError_t launch_geom_emit(const GeomParams& g, uint8_t* flags, const int2* bl
                              cudaStream_t s);
 
 // step.cu
+// The vectorised step kernel (csrc/step_vec.cu): lattices with nx a multiple of
+// step_vec_width(precision) and ny >= 8.
+int step_vec_width(int precision);
+bool step_vec_supported(int precision, int nx, int ny);
+cudaError_t launch_step_vec(int precision, const DevParams& p, const void* fa, void* fb,
+                            const uint8_t* flags, double* rho_m, double* ux_m, double* uy_m,
+                            bool fields_only, cudaStream_t s);
+// path: 0 = the vectorised kernel for the deviation formats where step_vec_supported(), else
+// the scalar tile kernel; 1 = the scalar tile kernel; 3 = the vectorised kernel where
+// step_vec_supported() (FP64 too)
 cudaError_t launch_step(int precision, const DevParams& p, const void* fa, void* fb,
                         const uint8_t* flags, double* rho_m, double* ux_m, double* uy_m,
-                        bool fields_only, cudaStream_t s);
+                        bool fields_only, cudaStream_t s, int path = 0);
 
 // boundary.cu
 // Per-link recipe of the wall pass, fixed at creation (depends on q, tau and the scheme only):
@@ -214,6 +224,7 @@ struct lbm_ctx {
   double T = 0.0;
   bool rho_ref_auto = false;  // deviation storage: take rho_ref from the initial state
   bool use_tma = false;       // step kernel with TMA halo staging (step_tma.cu)
+  int kernel_path = 0;        // lbm_options.kernel_path
   alignas(64) unsigned char tmap[2][128];  // tensor maps of the two lattices
   alignas(64) unsigned char fmap[128];     // tensor map of the node flags
 };

@@ -23,14 +23,103 @@ template <typename C>
 __device__ __forceinline__ C pop_sum(const C (&f)[9]) {
   C r = f[0];
 #pragma unroll
-  for (int a = 1; a < 9; ++a) r += f[a];
+  for (int a = 1; a < 9; ++a) r = r_add(r, f[a]);
   return r;
 }
 
-// Phase 2 of a tile: force (Eq. 16 from psi_s), velocity (Eq. 5), collision (Eq. 2) and push
-// (Eq. 3) of the RY nodes (x0 + tx, y0 + ty + TYN r) of this thread (TYN threads in y), given their populations f,
-// densities rho and flags fl; psi of the tile and its ring is in psi_s (complete: the caller
-// has synchronised the CTA).
+// The arithmetic of one fluid node (x, y): total force (Eq. 16 plus body forces) from the psi
+// differences of its opposite neighbours d13 = psi(x+1,y) - psi(x-1,y), d24 = psi(x,y+1) -
+// psi(x,y-1), d57 = psi(x+1,y+1) - psi(x-1,y-1), d86 = psi(x+1,y-1) - psi(x-1,y+1) and its own
+// psi; velocity with the half-force term (Eq. 5); BGK collision with Guo forcing (Eqs. 2, 4).
+// g: the node's nine stored values (deviations less w_a rho_ref for the deviation formats),
+// rh: its density.  st: the nine post-collision values as they will be stored (rounded to the
+// storage format).  Every operation is explicitly rounded, so all callers give the same bits.
+template <typename S, int EOS>
+__device__ __forceinline__ void collide_node(const DevParams& p,
+                                             const Consts<typename Pop<S>::C>& k,
+                                             const typename Pop<S>::C (&g)[9],
+                                             typename Pop<S>::C rh, typename Pop<S>::C d13,
+                                             typename Pop<S>::C d24, typename Pop<S>::C d57,
+                                             typename Pop<S>::C d86, typename Pop<S>::C psic,
+                                             int x, int y, typename Pop<S>::C (&st)[9],
+                                             typename Pop<S>::C& ux, typename Pop<S>::C& uy) {
+  using C = typename Pop<S>::C;
+  constexpr bool DEV = Pop<S>::dev;
+  const C rho_ref = DEV ? k.rho_ref : C(0);
+  C Fx = C(0), Fy = C(0);
+  if constexpr (EOS != LBM_EOS_NONE) {
+    // -G psi(x) sum_a w_a psi(x + e_a) e_a, as weighted differences of opposite neighbours (the
+    // subtractions of nearly equal psi are exact, which keeps FP32 forces accurate in smooth
+    // regions)
+    const C sx = r_fma(wpsi<C>(1), d13, r_mul(wpsi<C>(5), r_add(d57, d86)));
+    const C sy = r_fma(wpsi<C>(2), d24, r_mul(wpsi<C>(5), r_sub(d57, d86)));
+    const C mg = r_mul(-k.G, psic);
+    Fx = r_mul(mg, sx);
+    Fy = r_mul(mg, sy);
+  }
+  if (p.has_body) {
+    Fx = r_fma(rh, k.gx, Fx);
+    Fy = r_fma(rh, k.gy, Fy);
+    if (k.azC != C(0)) {
+      const C dx = r_sub(C(x), k.azcx), dy = r_sub(C(y), k.azcy);
+      const C r2 = r_fma(dx, dx, r_mul(dy, dy));
+      Fx = r_add(Fx, q_div(r_mul(k.azC, -dy), r2));
+      Fy = r_add(Fy, q_div(r_mul(k.azC, dx), r2));
+    }
+  }
+  // Velocity with the half-force term, Eq. (5).
+  const C mx = r_add(r_add(r_sub(g[1], g[3]), r_sub(g[5], g[7])), r_sub(g[8], g[6]));
+  const C my = r_add(r_add(r_sub(g[2], g[4]), r_sub(g[5], g[7])), r_sub(g[6], g[8]));
+  const C inv_rho = q_rcp(rh);
+  ux = r_mul(r_fma(C(0.5), Fx, mx), inv_rho);
+  uy = r_mul(r_fma(C(0.5), Fy, my), inv_rho);
+  // Collision, Eq. (2): f* = (1 - omega) f + omega f_eq + F_a, with f_eq of Eq. (4),
+  //   f_eq = w [c0 + rho eu (3 + 4.5 eu)],  c0 = rho (1 - 1.5 u.u) (less rho_ref if stored
+  //   as a deviation), and Guo's term F_a = w [K eF (1 + 3 eu) - K u.F], K = 3 (1 - 1/2tau),
+  //   eu = e_a.u, eF = e_a.F.
+  const C omega = k.omega, one_m_omega = k.one_m_omega, K = k.K;
+  const C uu = r_fma(ux, ux, r_mul(uy, uy));
+  const C c0 = r_fma(r_mul(C(-1.5), rh), uu, r_sub(rh, rho_ref));
+  const C uF = r_fma(ux, Fx, r_mul(uy, Fy));
+  const C A0 = r_fma(omega, c0, r_mul(-K, uF));
+  const C orho = r_mul(omega, rh);
+  // Opposite directions a, abar share |e.u| and |e.F|: h_a = P + Q, h_abar = P - Q with the
+  // even part P = A0 + (4.5 rho omega eu + 3 K eF) eu and the odd part Q = 3 rho omega eu + K eF.
+  C out[9];
+  out[0] = r_fma(one_m_omega, g[0], r_mul(wgt<C>(0), A0));
+  const C o45 = r_mul(C(4.5), orho), o3 = r_mul(C(3), orho), K3 = r_mul(C(3), K);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = i == 0 ? 1 : (i == 1 ? 2 : (i == 2 ? 5 : 6)), ab = opposite(a);
+    // e_a = (1,0), (0,1), (1,1), (-1,1)
+    const C eu = i == 0 ? ux : (i == 1 ? uy : (i == 2 ? r_add(ux, uy) : r_sub(uy, ux)));
+    const C eF = i == 0 ? Fx : (i == 1 ? Fy : (i == 2 ? r_add(Fx, Fy) : r_sub(Fy, Fx)));
+    const C P = r_fma(r_fma(o45, eu, r_mul(K3, eF)), eu, A0);
+    const C Q = r_fma(o3, eu, r_mul(K, eF));
+    const C w = wgt<C>(a);
+    out[a] = r_fma(one_m_omega, g[a], r_mul(w, r_add(P, Q)));
+    out[ab] = r_fma(one_m_omega, g[ab], r_mul(w, r_sub(P, Q)));
+  }
+#pragma unroll
+  for (int a = 0; a < 9; ++a) st[a] = Pop<S>::rounded(a, out[a]);
+  if constexpr (DEV) {
+    // The collision conserves mass exactly (sum of f_eq is rho, sum of the Guo term is 0), but
+    // rounding the nine results does not, and near a steady state the rounding repeats every
+    // step, so mass would drift linearly.  The rest population therefore takes the node's
+    // stored mass minus the eight rounded moving populations, written as
+    // g_0 + sum_a (g_a - g*_a) so that only small differences are added.
+    C d = C(0);
+#pragma unroll
+    for (int a = 1; a < 9; ++a) d = r_add(d, r_sub(g[a], st[a]));
+    st[0] = r_add(g[0], d);
+  }
+}
+
+// Phase 2 of a tile: the nodes (x0 + tx, y0 + ty + TYN r) of this thread (TYN threads in y),
+// given their populations f, densities rho and flags fl; psi of the tile and its ring is in
+// psi_s (complete: the caller has synchronised the CTA).  Writes the moments of FLAG_MACRO nodes
+// for the wall pass (FIELDS: the moments of every node instead) and pushes (Eq. 3) the
+// post-collision populations to x + e_a of fb.
 template <typename S, int EOS, bool FIELDS, int RY, int TYN = TYT>
 __device__ __forceinline__ void tile_phase2(const DevParams& p, void* __restrict__ fb,
                                             double* __restrict__ rho_m,
@@ -46,10 +135,7 @@ __device__ __forceinline__ void tile_phase2(const DevParams& p, void* __restrict
   const int nx = p.nx, ny = p.ny;
   const int N = p.N;
   const Consts<C>& k = p.k<C>();
-  const C rho_ref = DEV ? k.rho_ref : C(0);
   const int x = x0 + tx;
-  const C omega = k.omega, one_m_omega = k.one_m_omega;
-  const C K = k.K;  // 3 (1 - 1/(2 tau)): Guo prefactor times 1/c_s^2
   const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
@@ -65,97 +151,32 @@ __device__ __forceinline__ void tile_phase2(const DevParams& p, void* __restrict
       }
       continue;
     }
-    const C rh = rho[r];
-    // Total force: Eq. (16) plus body forces.
-    C Fx = C(0), Fy = C(0);
+    const int cx = tx + 1, cy = ty + r * TYN + 1;
+    C d13 = C(0), d24 = C(0), d57 = C(0), d86 = C(0), psic = C(0);
     if constexpr (EOS != LBM_EOS_NONE) {
-      const int cx = tx + 1, cy = ty + r * TYN + 1;
-      // sum_a w_a psi(x + e_a) e_a as weighted differences of opposite neighbours: the
-      // subtractions of nearly equal psi are exact, which keeps FP32 forces accurate in smooth
-      // regions
-      const C d13 = psi_s[cy][cx + 1] - psi_s[cy][cx - 1];
-      const C d24 = psi_s[cy + 1][cx] - psi_s[cy - 1][cx];
-      const C d57 = psi_s[cy + 1][cx + 1] - psi_s[cy - 1][cx - 1];
-      const C d86 = psi_s[cy - 1][cx + 1] - psi_s[cy + 1][cx - 1];
-      const C sx = wpsi<C>(1) * d13 + wpsi<C>(5) * (d57 + d86);
-      const C sy = wpsi<C>(2) * d24 + wpsi<C>(5) * (d57 - d86);
-      const C mg = -k.G * psi_s[cy][cx];
-      Fx = mg * sx;
-      Fy = mg * sy;
+      d13 = r_sub(psi_s[cy][cx + 1], psi_s[cy][cx - 1]);
+      d24 = r_sub(psi_s[cy + 1][cx], psi_s[cy - 1][cx]);
+      d57 = r_sub(psi_s[cy + 1][cx + 1], psi_s[cy - 1][cx - 1]);
+      d86 = r_sub(psi_s[cy - 1][cx + 1], psi_s[cy + 1][cx - 1]);
+      psic = psi_s[cy][cx];
     }
-    if (p.has_body) {
-      Fx += rh * k.gx;
-      Fy += rh * k.gy;
-      if (k.azC != C(0)) {
-        const C dx = C(x) - k.azcx, dy = C(y) - k.azcy;
-        const C r2 = dx * dx + dy * dy;
-        Fx += k.azC * (-dy) / r2;
-        Fy += k.azC * dx / r2;
-      }
-    }
-    const C(&g)[9] = f[r];
-    // Velocity with the half-force term, Eq. (5).
-    const C mx = ((g[1] - g[3]) + (g[5] - g[7])) + (g[8] - g[6]);
-    const C my = ((g[2] - g[4]) + (g[5] - g[7])) + (g[6] - g[8]);
-    const C inv_rho = q_rcp(rh);
-    const C ux = (mx + C(0.5) * Fx) * inv_rho;
-    const C uy = (my + C(0.5) * Fy) * inv_rho;
+    C st[9], ux, uy;
+    collide_node<S, EOS>(p, k, f[r], rho[r], d13, d24, d57, d86, psic, x, y, st, ux, uy);
     if constexpr (FIELDS) {
-      rho_m[n] = double(rh);
+      rho_m[n] = double(rho[r]);
       ux_m[n] = double(ux);
       uy_m[n] = double(uy);
-      continue;
     } else {
       if (fl[r] & FLAG_MACRO) {  // for the wall pass, in its arithmetic type
         if constexpr (DEV) {
-          reinterpret_cast<float*>(rho_m)[n] = rh;
+          reinterpret_cast<float*>(rho_m)[n] = rho[r];
           reinterpret_cast<float*>(ux_m)[n] = ux;
           reinterpret_cast<float*>(uy_m)[n] = uy;
         } else {
-          rho_m[n] = rh;
+          rho_m[n] = rho[r];
           ux_m[n] = ux;
           uy_m[n] = uy;
         }
-      }
-      // Collision, Eq. (2): f* = (1 - omega) f + omega f_eq + F_a, with f_eq of Eq. (4),
-      //   f_eq = w [c0 + rho eu (3 + 4.5 eu)],  c0 = rho (1 - 1.5 u.u) (less rho_ref if stored
-      //   as a deviation), and Guo's term F_a = w [K eF (1 + 3 eu) - K u.F], K = 3 (1 - 1/2tau),
-      //   eu = e_a.u, eF = e_a.F.
-      const C uu = ux * ux + uy * uy;
-      const C c0 = (rh - rho_ref) - C(1.5) * rh * uu;
-      const C uF = ux * Fx + uy * Fy;
-      const C A0 = omega * c0 - K * uF;
-      const C orho = omega * rh;
-      // Opposite directions a, abar share |e.u| and |e.F|: h_a = P + Q, h_abar = P - Q with the
-      // even part P = A0 + 4.5 rho omega eu^2 + 3 K eF eu and the odd part
-      // Q = 3 rho omega eu + K eF.
-      C out[9];
-      out[0] = one_m_omega * g[0] + wgt<C>(0) * A0;
-      const C o45 = C(4.5) * orho, o3 = C(3) * orho, K3 = C(3) * K;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int a = i == 0 ? 1 : (i == 1 ? 2 : (i == 2 ? 5 : 6)), ab = opposite(a);
-        const C eu = (ex(a) ? C(ex(a)) * ux : C(0)) + (ey(a) ? C(ey(a)) * uy : C(0));
-        const C eF = (ex(a) ? C(ex(a)) * Fx : C(0)) + (ey(a) ? C(ey(a)) * Fy : C(0));
-        const C P = A0 + (o45 * eu + K3 * eF) * eu;
-        const C Q = o3 * eu + K * eF;
-        const C w = wgt<C>(a);
-        out[a] = one_m_omega * g[a] + w * (P + Q);
-        out[ab] = one_m_omega * g[ab] + w * (P - Q);
-      }
-      C st[9];  // the values as stored (rounded to the storage format)
-#pragma unroll
-      for (int a = 0; a < 9; ++a) st[a] = Pop<S>::rounded(a, out[a]);
-      if constexpr (DEV) {
-        // The collision conserves mass exactly (sum of f_eq is rho, sum of the Guo term is 0),
-        // but rounding the nine FP32 results does not, and near a steady state the rounding
-        // repeats every step, so mass would drift linearly.  The rest population therefore
-        // takes the node's stored mass minus the eight rounded moving populations, written as
-        // g_0 + sum_a (g_a - g*_a) so that only small differences are added.
-        C d = C(0);
-#pragma unroll
-        for (int a = 1; a < 9; ++a) d += g[a] - st[a];
-        st[0] = g[0] + d;
       }
       const int row = y * nx;
       const int rowp = (y + 1 == ny ? 0 : y + 1) * nx, rowm = (y == 0 ? ny - 1 : y - 1) * nx;
@@ -249,15 +270,15 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
     }
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
-      if (!(fl[r] & FLAG_SOLID)) rho[r] = rho_ref + pop_sum<C>(f[r]);
+      if (!(fl[r] & FLAG_SOLID)) rho[r] = r_add(rho_ref, pop_sum<C>(f[r]));
       psi_s[ty + r * TYT + 1][tx + 1] = (fl[r] & FLAG_SOLID) ? psi_w : psi_of<C, EOS>(k, rho[r]);
     }
-    if (c < kRing) psi_s[hy][hx] = ring_fluid ? psi_of<C, EOS>(k, rho_ref + pop_sum<C>(v)) : psi_w;
+    if (c < kRing) psi_s[hy][hx] = ring_fluid ? psi_of<C, EOS>(k, r_add(rho_ref, pop_sum<C>(v))) : psi_w;
     __syncthreads();
   } else {
 #pragma unroll
     for (int r = 0; r < RY; ++r)
-      if (!(fl[r] & FLAG_SOLID)) rho[r] = rho_ref + pop_sum<C>(f[r]);
+      if (!(fl[r] & FLAG_SOLID)) rho[r] = r_add(rho_ref, pop_sum<C>(f[r]));
   }
 
   tile_phase2<S, EOS, FIELDS, RY>(p, fb, rho_m, ux_m, uy_m, x0, y0, psi_s, f, rho, fl);

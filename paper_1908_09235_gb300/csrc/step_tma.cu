@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(TX* TYM, 2)
       fl[r] = sfl[row * FW + tx + 16];
 #pragma unroll
       for (int a = 0; a < 9; ++a) f[r][a] = st[a * PLANE + row * SW + tx + 4];
-      rho[r] = (fl[r] & FLAG_SOLID) ? C(1) : rho_ref + pop_sum<C>(f[r]);
+      rho[r] = (fl[r] & FLAG_SOLID) ? C(1) : r_add(rho_ref, pop_sum<C>(f[r]));
       if constexpr (EOS != LBM_EOS_NONE)
         psi_s[row][tx + 1] = (fl[r] & FLAG_SOLID) ? psi_w : psi_of<C, EOS>(k, rho[r]);
     }
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(TX* TYM, 2)
           C v[9];
 #pragma unroll
           for (int a = 0; a < 9; ++a) v[a] = st[a * PLANE + hy * SW + hx + 3];
-          ps = psi_of<C, EOS>(k, rho_ref + pop_sum<C>(v));
+          ps = psi_of<C, EOS>(k, r_add(rho_ref, pop_sum<C>(v)));
         }
         psi_s[hy][hx] = ps;
       }
