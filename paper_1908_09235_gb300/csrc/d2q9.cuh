@@ -147,6 +147,22 @@ struct Pop<__half> {
   }
 };
 
+// Lane types of the per-node arithmetic: one node (float, double) or two nodes packed in the
+// f32x2 registers of Blackwell's paired FP32 instructions (float2).  Elem<L>::C is the element
+// type; splat() broadcasts a scalar.
+template <typename L>
+struct Elem;
+template <>
+struct Elem<float> { using C = float; static constexpr int W = 1; };
+template <>
+struct Elem<double> { using C = double; static constexpr int W = 1; };
+template <>
+struct Elem<float2> { using C = float; static constexpr int W = 2; };
+template <typename L>
+__device__ __forceinline__ L splat(typename Elem<L>::C c) {
+  if constexpr (Elem<L>::W == 2) return make_float2(c, c); else return c;
+}
+
 // psi(rho): exponential psi0 exp(-rho0/rho) (Sec. 3.2) or the Carnahan-Starling form
 // sqrt(2 (p - rho/3)/G); zero for a single-phase fluid.
 // Division, reciprocal, square root and exponential in the arithmetic type: correctly rounded
@@ -154,40 +170,55 @@ struct Pop<__half> {
 // FP32 error budget of the method's steady state) to keep the FP32 step memory-bound.
 __device__ __forceinline__ double q_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float q_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float2 q_div(float2 a, float2 b) {
+  return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+}
 __device__ __forceinline__ double q_rcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ float q_rcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ float2 q_rcp(float2 a) { return make_float2(q_rcp(a.x), q_rcp(a.y)); }
 __device__ __forceinline__ double q_sqrt(double a) { return sqrt(a); }
-__device__ __forceinline__ float q_sqrt(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
+__device__ __forceinline__ float q_sqrt(float a) { return a > 0.f ? __fmul_rn(a, rsqrtf(a)) : 0.f; }
+__device__ __forceinline__ float2 q_sqrt(float2 a) { return make_float2(q_sqrt(a.x), q_sqrt(a.y)); }
 __device__ __forceinline__ double q_exp(double a) { return exp(a); }
 __device__ __forceinline__ float q_exp(float a) { return __expf(a); }
+__device__ __forceinline__ float2 q_exp(float2 a) { return make_float2(__expf(a.x), __expf(a.y)); }
 
 // Explicitly rounded arithmetic (no contraction freedom for the compiler): every kernel that
 // inlines the per-node arithmetic (the scalar and the vectorised tile cores, the batched kernel)
-// then produces the same bits for the same node.
+// then produces the same bits for the same node.  The paired FP32 forms round each element
+// exactly as the scalar ones; a - b is fma(b, -1, a), the same single rounding of a - b.
 __device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float2 r_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float2 r_sub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
 __device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float2 r_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float2 r_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-template <typename C, int EOS>
-__device__ __forceinline__ C psi_of(const Consts<C>& k, C rho) {
+template <typename C, int EOS, typename L>
+__device__ __forceinline__ L psi_of(const Consts<C>& k, L rho) {
   if constexpr (EOS == LBM_EOS_EXP) {
-    return r_mul(k.psi0, q_exp(-q_div(k.rho0, rho)));
+    return r_mul(splat<L>(k.psi0), q_exp(r_mul(splat<L>(C(-1)), q_div(splat<L>(k.rho0), rho))));
   } else if constexpr (EOS == LBM_EOS_CS) {
     // p = rho R T (1 + eta + eta^2 - eta^3) / (1 - eta)^3 - a rho^2,  eta = b rho / 4
-    const C eta = r_mul(k.b4, rho);
-    const C om = r_sub(C(1), eta);
-    const C e2 = r_mul(eta, eta);
-    const C num = r_sub(r_add(r_add(C(1), eta), e2), r_mul(e2, eta));
-    const C om3 = r_mul(r_mul(om, om), om);
-    const C pr = r_sub(q_div(r_mul(r_mul(rho, k.RT), num), om3), r_mul(r_mul(k.a, rho), rho));
-    return q_sqrt(r_mul(r_sub(pr, r_mul(rho, C(1.0 / 3.0))), k.two_over_G));
+    const L one = splat<L>(C(1));
+    const L eta = r_mul(splat<L>(k.b4), rho);
+    const L om = r_sub(one, eta);
+    const L e2 = r_mul(eta, eta);
+    const L num = r_sub(r_add(r_add(one, eta), e2), r_mul(e2, eta));
+    const L om3 = r_mul(r_mul(om, om), om);
+    const L pr = r_sub(q_div(r_mul(r_mul(rho, splat<L>(k.RT)), num), om3),
+                       r_mul(r_mul(splat<L>(k.a), rho), rho));
+    return q_sqrt(r_mul(r_sub(pr, r_mul(rho, splat<L>(C(1.0 / 3.0)))), splat<L>(k.two_over_G)));
   } else {
-    return C(0);
+    return splat<L>(C(0));
   }
 }
 

@@ -27,88 +27,96 @@ __device__ __forceinline__ C pop_sum(const C (&f)[9]) {
   return r;
 }
 
-// The arithmetic of one fluid node (x, y): total force (Eq. 16 plus body forces) from the psi
-// differences of its opposite neighbours d13 = psi(x+1,y) - psi(x-1,y), d24 = psi(x,y+1) -
-// psi(x,y-1), d57 = psi(x+1,y+1) - psi(x-1,y-1), d86 = psi(x+1,y-1) - psi(x-1,y+1) and its own
-// psi; velocity with the half-force term (Eq. 5); BGK collision with Guo forcing (Eqs. 2, 4).
-// g: the node's nine stored values (deviations less w_a rho_ref for the deviation formats),
-// rh: its density.  st: the nine post-collision values as they will be stored (rounded to the
-// storage format).  Every operation is explicitly rounded, so all callers give the same bits.
-template <typename S, int EOS>
+// A post-collision value rounded to the storage format of plane a (per element).
+template <typename S, typename L>
+__device__ __forceinline__ L round_st(int a, L v) {
+  if constexpr (Elem<L>::W == 2)
+    return make_float2(Pop<S>::rounded(a, v.x), Pop<S>::rounded(a, v.y));
+  else
+    return Pop<S>::rounded(a, v);
+}
+
+// The arithmetic of one fluid node (x, y), or of two nodes at once when L is float2 (the paired
+// FP32 instructions; each element is rounded exactly as alone): total force (Eq. 16 plus body
+// forces) from the psi differences of its opposite neighbours d13 = psi(x+1,y) - psi(x-1,y),
+// d24 = psi(x,y+1) - psi(x,y-1), d57 = psi(x+1,y+1) - psi(x-1,y-1), d86 = psi(x+1,y-1) -
+// psi(x-1,y+1) and its own psi; velocity with the half-force term (Eq. 5); BGK collision with
+// Guo forcing (Eqs. 2, 4).  g: the node's nine stored values (deviations less w_a rho_ref for
+// the deviation formats), rh: its density, xf, yf: its coordinates.  st: the nine post-collision
+// values as they will be stored (rounded to the storage format).  Every operation is explicitly
+// rounded, so all callers give the same bits.
+template <typename S, int EOS, typename L>
 __device__ __forceinline__ void collide_node(const DevParams& p,
                                              const Consts<typename Pop<S>::C>& k,
-                                             const typename Pop<S>::C (&g)[9],
-                                             typename Pop<S>::C rh, typename Pop<S>::C d13,
-                                             typename Pop<S>::C d24, typename Pop<S>::C d57,
-                                             typename Pop<S>::C d86, typename Pop<S>::C psic,
-                                             int x, int y, typename Pop<S>::C (&st)[9],
-                                             typename Pop<S>::C& ux, typename Pop<S>::C& uy) {
+                                             const L (&g)[9], L rh, L d13, L d24, L d57, L d86,
+                                             L psic, L xf, L yf, L (&st)[9], L& ux, L& uy) {
   using C = typename Pop<S>::C;
   constexpr bool DEV = Pop<S>::dev;
-  const C rho_ref = DEV ? k.rho_ref : C(0);
-  C Fx = C(0), Fy = C(0);
+  auto c_ = [](C v) { return splat<L>(v); };
+  const L rho_ref = c_(DEV ? k.rho_ref : C(0));
+  L Fx = c_(C(0)), Fy = c_(C(0));
   if constexpr (EOS != LBM_EOS_NONE) {
     // -G psi(x) sum_a w_a psi(x + e_a) e_a, as weighted differences of opposite neighbours (the
     // subtractions of nearly equal psi are exact, which keeps FP32 forces accurate in smooth
     // regions)
-    const C sx = r_fma(wpsi<C>(1), d13, r_mul(wpsi<C>(5), r_add(d57, d86)));
-    const C sy = r_fma(wpsi<C>(2), d24, r_mul(wpsi<C>(5), r_sub(d57, d86)));
-    const C mg = r_mul(-k.G, psic);
+    const L sx = r_fma(c_(wpsi<C>(1)), d13, r_mul(c_(wpsi<C>(5)), r_add(d57, d86)));
+    const L sy = r_fma(c_(wpsi<C>(2)), d24, r_mul(c_(wpsi<C>(5)), r_sub(d57, d86)));
+    const L mg = r_mul(c_(-k.G), psic);
     Fx = r_mul(mg, sx);
     Fy = r_mul(mg, sy);
   }
   if (p.has_body) {
-    Fx = r_fma(rh, k.gx, Fx);
-    Fy = r_fma(rh, k.gy, Fy);
+    Fx = r_fma(rh, c_(k.gx), Fx);
+    Fy = r_fma(rh, c_(k.gy), Fy);
     if (k.azC != C(0)) {
-      const C dx = r_sub(C(x), k.azcx), dy = r_sub(C(y), k.azcy);
-      const C r2 = r_fma(dx, dx, r_mul(dy, dy));
-      Fx = r_add(Fx, q_div(r_mul(k.azC, -dy), r2));
-      Fy = r_add(Fy, q_div(r_mul(k.azC, dx), r2));
+      const L dx = r_sub(xf, c_(k.azcx)), dy = r_sub(yf, c_(k.azcy));
+      const L r2 = r_fma(dx, dx, r_mul(dy, dy));
+      Fx = r_add(Fx, q_div(r_mul(c_(-k.azC), dy), r2));
+      Fy = r_add(Fy, q_div(r_mul(c_(k.azC), dx), r2));
     }
   }
   // Velocity with the half-force term, Eq. (5).
-  const C mx = r_add(r_add(r_sub(g[1], g[3]), r_sub(g[5], g[7])), r_sub(g[8], g[6]));
-  const C my = r_add(r_add(r_sub(g[2], g[4]), r_sub(g[5], g[7])), r_sub(g[6], g[8]));
-  const C inv_rho = q_rcp(rh);
-  ux = r_mul(r_fma(C(0.5), Fx, mx), inv_rho);
-  uy = r_mul(r_fma(C(0.5), Fy, my), inv_rho);
+  const L mx = r_add(r_add(r_sub(g[1], g[3]), r_sub(g[5], g[7])), r_sub(g[8], g[6]));
+  const L my = r_add(r_add(r_sub(g[2], g[4]), r_sub(g[5], g[7])), r_sub(g[6], g[8]));
+  const L inv_rho = q_rcp(rh);
+  ux = r_mul(r_fma(c_(C(0.5)), Fx, mx), inv_rho);
+  uy = r_mul(r_fma(c_(C(0.5)), Fy, my), inv_rho);
   // Collision, Eq. (2): f* = (1 - omega) f + omega f_eq + F_a, with f_eq of Eq. (4),
   //   f_eq = w [c0 + rho eu (3 + 4.5 eu)],  c0 = rho (1 - 1.5 u.u) (less rho_ref if stored
   //   as a deviation), and Guo's term F_a = w [K eF (1 + 3 eu) - K u.F], K = 3 (1 - 1/2tau),
   //   eu = e_a.u, eF = e_a.F.
-  const C omega = k.omega, one_m_omega = k.one_m_omega, K = k.K;
-  const C uu = r_fma(ux, ux, r_mul(uy, uy));
-  const C c0 = r_fma(r_mul(C(-1.5), rh), uu, r_sub(rh, rho_ref));
-  const C uF = r_fma(ux, Fx, r_mul(uy, Fy));
-  const C A0 = r_fma(omega, c0, r_mul(-K, uF));
-  const C orho = r_mul(omega, rh);
+  const L omega = c_(k.omega), one_m_omega = c_(k.one_m_omega), K = c_(k.K);
+  const L uu = r_fma(ux, ux, r_mul(uy, uy));
+  const L c0 = r_fma(r_mul(c_(C(-1.5)), rh), uu, r_sub(rh, rho_ref));
+  const L uF = r_fma(ux, Fx, r_mul(uy, Fy));
+  const L A0 = r_fma(omega, c0, r_mul(c_(-k.K), uF));
+  const L orho = r_mul(omega, rh);
   // Opposite directions a, abar share |e.u| and |e.F|: h_a = P + Q, h_abar = P - Q with the
   // even part P = A0 + (4.5 rho omega eu + 3 K eF) eu and the odd part Q = 3 rho omega eu + K eF.
-  C out[9];
-  out[0] = r_fma(one_m_omega, g[0], r_mul(wgt<C>(0), A0));
-  const C o45 = r_mul(C(4.5), orho), o3 = r_mul(C(3), orho), K3 = r_mul(C(3), K);
+  L out[9];
+  out[0] = r_fma(one_m_omega, g[0], r_mul(c_(wgt<C>(0)), A0));
+  const L o45 = r_mul(c_(C(4.5)), orho), o3 = r_mul(c_(C(3)), orho), K3 = r_mul(c_(C(3)), K);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int a = i == 0 ? 1 : (i == 1 ? 2 : (i == 2 ? 5 : 6)), ab = opposite(a);
     // e_a = (1,0), (0,1), (1,1), (-1,1)
-    const C eu = i == 0 ? ux : (i == 1 ? uy : (i == 2 ? r_add(ux, uy) : r_sub(uy, ux)));
-    const C eF = i == 0 ? Fx : (i == 1 ? Fy : (i == 2 ? r_add(Fx, Fy) : r_sub(Fy, Fx)));
-    const C P = r_fma(r_fma(o45, eu, r_mul(K3, eF)), eu, A0);
-    const C Q = r_fma(o3, eu, r_mul(K, eF));
-    const C w = wgt<C>(a);
+    const L eu = i == 0 ? ux : (i == 1 ? uy : (i == 2 ? r_add(ux, uy) : r_sub(uy, ux)));
+    const L eF = i == 0 ? Fx : (i == 1 ? Fy : (i == 2 ? r_add(Fx, Fy) : r_sub(Fy, Fx)));
+    const L P = r_fma(r_fma(o45, eu, r_mul(K3, eF)), eu, A0);
+    const L Q = r_fma(o3, eu, r_mul(K, eF));
+    const L w = c_(wgt<C>(a));
     out[a] = r_fma(one_m_omega, g[a], r_mul(w, r_add(P, Q)));
     out[ab] = r_fma(one_m_omega, g[ab], r_mul(w, r_sub(P, Q)));
   }
 #pragma unroll
-  for (int a = 0; a < 9; ++a) st[a] = Pop<S>::rounded(a, out[a]);
+  for (int a = 0; a < 9; ++a) st[a] = round_st<S>(a, out[a]);
   if constexpr (DEV) {
     // The collision conserves mass exactly (sum of f_eq is rho, sum of the Guo term is 0), but
     // rounding the nine results does not, and near a steady state the rounding repeats every
     // step, so mass would drift linearly.  The rest population therefore takes the node's
     // stored mass minus the eight rounded moving populations, written as
     // g_0 + sum_a (g_a - g*_a) so that only small differences are added.
-    C d = C(0);
+    L d = c_(C(0));
 #pragma unroll
     for (int a = 1; a < 9; ++a) d = r_add(d, r_sub(g[a], st[a]));
     st[0] = r_add(g[0], d);
@@ -161,7 +169,7 @@ __device__ __forceinline__ void tile_phase2(const DevParams& p, void* __restrict
       psic = psi_s[cy][cx];
     }
     C st[9], ux, uy;
-    collide_node<S, EOS>(p, k, f[r], rho[r], d13, d24, d57, d86, psic, x, y, st, ux, uy);
+    collide_node<S, EOS>(p, k, f[r], rho[r], d13, d24, d57, d86, psic, C(x), C(y), st, ux, uy);
     if constexpr (FIELDS) {
       rho_m[n] = double(rho[r]);
       ux_m[n] = double(ux);

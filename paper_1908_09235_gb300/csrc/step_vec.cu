@@ -23,6 +23,8 @@
 //
 // The per-node arithmetic is collide_node() and psi_of(), explicitly rounded, so a node gets the
 // same bits here, in the scalar tile kernel and in the batched kernel.
+#include <type_traits>
+
 #include "step_core.cuh"
 
 namespace lbm {
@@ -166,6 +168,16 @@ struct Vec<__half> {
   }
 };
 
+// lane values: element e of a packed pair, and packing (a single node ignores the second)
+template <typename L>
+__device__ __forceinline__ typename Elem<L>::C el(const L& x, int e) {
+  if constexpr (Elem<L>::W == 2) return e == 0 ? x.x : x.y; else return x;
+}
+template <typename L>
+__device__ __forceinline__ L pack(typename Elem<L>::C a, typename Elem<L>::C b) {
+  if constexpr (Elem<L>::W == 2) return make_float2(a, b); else return a;
+}
+
 template <int V>
 __device__ __forceinline__ void load_flags(const uint8_t* flags, int n, uint8_t (&o)[V]) {
   if constexpr (V == 4) {
@@ -291,7 +303,10 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
   const int y = y0 + w, yo = wrapy(y);
   const bool lane_ok = lane < nv;
   const int n = yo * nx + x0 + V * (lane_ok ? lane : 0);
-  C f[V][9];
+  // the lane's V nodes as NP lane values of W nodes (FP32 arithmetic: pairs in f32x2 registers)
+  using L = std::conditional_t<sizeof(C) == 4, float2, C>;
+  constexpr int W = Elem<L>::W, NP = V / W;
+  L f[NP][9];
   uint8_t fl[V];
   load_flags<V>(flags, n, fl);
 #pragma unroll
@@ -299,16 +314,24 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
     C t[V];
     VT::load(fa, a, N, n, t);
 #pragma unroll
-    for (int v = 0; v < V; ++v) f[v][a] = t[v];
+    for (int q = 0; q < NP; ++q) f[q][a] = pack<L>(t[W * q], t[W * q + W - 1]);
   }
 
-  C rho[V];
+  L rho[NP];
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const bool solid = fl[v] & FLAG_SOLID;
-    rho[v] = solid ? C(1) : r_add(rho_ref, pop_sum<C>(f[v]));
+  for (int q = 0; q < NP; ++q) {
+    const L r = r_add(splat<L>(rho_ref), pop_sum<L>(f[q]));
+    C re[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) re[e] = (fl[W * q + e] & FLAG_SOLID) ? C(1) : el(r, e);
+    rho[q] = pack<L>(re[0], re[W - 1]);
     if constexpr (PSI) {
-      if (lane_ok) psi_s[w + 1][pj(V * (lane + 1) + v)] = solid ? psi_w : psi_of<C, EOS>(k, rho[v]);
+      const L ps = psi_of<C, EOS>(k, rho[q]);
+#pragma unroll
+      for (int e = 0; e < W; ++e)
+        if (lane_ok)
+          psi_s[w + 1][pj(V * (lane + 1) + W * q + e)] =
+              (fl[W * q + e] & FLAG_SOLID) ? psi_w : el(ps, e);
     }
   }
   if constexpr (PSI) {
@@ -363,52 +386,57 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
     const int j = v + dx;          // -1 .. V
     return j < 0 ? -2 : (j < V ? j : V + 1);
   };
-  auto diffs = [&](int v, C& d13, C& d24, C& d57, C& d86, C& psic) {
+  // psi values of lane value q (nodes W q .. W q + W - 1) at x-offset dx in row rr
+  auto psi_at = [&](const C* rr, int q, int dx) {
+    return pack<L>(rr[pcol(W * q, dx)], rr[pcol(W * q + W - 1, dx)]);
+  };
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    L d13, d24, d57, d86, psic;
     if constexpr (PSI) {
       const C* rm = &psi_s[w][pbase];
       const C* r0 = &psi_s[w + 1][pbase];
       const C* rp = &psi_s[w + 2][pbase];
-      const int cm = pcol(v, -1), c0 = pcol(v, 0), cp = pcol(v, 1);
-      d13 = r_sub(r0[cp], r0[cm]);
-      d24 = r_sub(rp[c0], rm[c0]);
-      d57 = r_sub(rp[cp], rm[cm]);
-      d86 = r_sub(rm[cp], rp[cm]);
-      psic = r0[c0];
+      d13 = r_sub(psi_at(r0, q, 1), psi_at(r0, q, -1));
+      d24 = r_sub(psi_at(rp, q, 0), psi_at(rm, q, 0));
+      d57 = r_sub(psi_at(rp, q, 1), psi_at(rm, q, -1));
+      d86 = r_sub(psi_at(rm, q, 1), psi_at(rp, q, -1));
+      psic = psi_at(r0, q, 0);
     } else {
-      d13 = d24 = d57 = d86 = psic = C(0);
+      d13 = d24 = d57 = d86 = psic = splat<L>(C(0));
     }
-  };
+    const int x = x0 + V * lane + W * q;
+    L st[9], ux, uy;
+    collide_node<S, EOS, L>(p, k, f[q], rho[q], d13, d24, d57, d86, psic,
+                            pack<L>(C(x), C(x + W - 1)), splat<L>(C(yo)), st, ux, uy);
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const int x = x0 + V * lane + v;
-    const int nn = yo * nx + x;
-    const bool solid = fl[v] & FLAG_SOLID;
-    C d13, d24, d57, d86, psic;
-    diffs(v, d13, d24, d57, d86, psic);
-    C st[9], ux, uy;
-    collide_node<S, EOS>(p, k, f[v], rho[v], d13, d24, d57, d86, psic, x, yo, st, ux, uy);
-    if constexpr (FIELDS) {
-      if (lane_ok) {
-        const double nan = __longlong_as_double(0x7ff8000000000000LL);
-        rho_m[nn] = solid ? nan : double(rho[v]);
-        ux_m[nn] = solid ? nan : double(ux);
-        uy_m[nn] = solid ? nan : double(uy);
-      }
-    } else {
-      if (lane_ok && (fl[v] & FLAG_MACRO)) {  // for the wall pass (fluid nodes only)
+    for (int e = 0; e < W; ++e) {
+      const int nn = yo * nx + x + e;
+      const uint8_t fe = fl[W * q + e];
+      if constexpr (FIELDS) {
+        if (lane_ok) {
+          const double nan = __longlong_as_double(0x7ff8000000000000LL);
+          const bool solid = fe & FLAG_SOLID;
+          rho_m[nn] = solid ? nan : double(el(rho[q], e));
+          ux_m[nn] = solid ? nan : double(el(ux, e));
+          uy_m[nn] = solid ? nan : double(el(uy, e));
+        }
+      } else if (lane_ok && (fe & FLAG_MACRO)) {  // for the wall pass (fluid nodes only)
         if constexpr (DEV) {
-          reinterpret_cast<float*>(rho_m)[nn] = rho[v];
-          reinterpret_cast<float*>(ux_m)[nn] = ux;
-          reinterpret_cast<float*>(uy_m)[nn] = uy;
+          reinterpret_cast<float*>(rho_m)[nn] = el(rho[q], e);
+          reinterpret_cast<float*>(ux_m)[nn] = el(ux, e);
+          reinterpret_cast<float*>(uy_m)[nn] = el(uy, e);
         } else {
-          rho_m[nn] = rho[v];
-          ux_m[nn] = ux;
-          uy_m[nn] = uy;
+          rho_m[nn] = el(rho[q], e);
+          ux_m[nn] = el(ux, e);
+          uy_m[nn] = el(uy, e);
         }
       }
-      // (a solid node's values go to slots nothing reads or the wall pass overwrites)
+    }
+    // (a solid node's values go to slots nothing reads or the wall pass overwrites)
+    if constexpr (!FIELDS) {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) f[v][a] = st[a];
+      for (int a = 0; a < 9; ++a) f[q][a] = st[a];
     }
   }
   if constexpr (FIELDS) return;
@@ -420,18 +448,19 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
   const int col = x0 + V * (lane_ok ? lane : 0);
   const int col_l = wrapx(x0 - 1), col_r = wrapx(x0 + V * nv);
   const bool first = lane == 0, last = lane == nv - 1;
+  auto fv = [&](int v, int a) { return el(f[v / W][a], v % W); };  // node v's value, plane a
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const int d = (ey(a) > 0 ? rowp : (ey(a) < 0 ? rowm : row0));
     C out[V];
     if (ex(a) == 0) {
 #pragma unroll
-      for (int v = 0; v < V; ++v) out[v] = f[v][a];
+      for (int v = 0; v < V; ++v) out[v] = fv(v, a);
       if (lane_ok) VT::store(fb, a, N, d + col, out);
     } else if (ex(a) > 0) {
-      out[0] = __shfl_up_sync(0xffffffffu, f[V - 1][a], 1);
+      out[0] = __shfl_up_sync(0xffffffffu, fv(V - 1, a), 1);
 #pragma unroll
-      for (int v = 1; v < V; ++v) out[v] = f[v - 1][a];
+      for (int v = 1; v < V; ++v) out[v] = fv(v - 1, a);
       if (lane_ok && !first) VT::store(fb, a, N, d + col, out);
       if (first) {  // elements 1 .. V - 1
         if constexpr (V == 4) {
@@ -441,11 +470,11 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
           VT::store1(fb, a, N, d + col + 1, out[1]);
         }
       }
-      if (last) VT::store1(fb, a, N, d + col_r, f[V - 1][a]);
+      if (last) VT::store1(fb, a, N, d + col_r, fv(V - 1, a));
     } else {
-      out[V - 1] = __shfl_down_sync(0xffffffffu, f[0][a], 1);
+      out[V - 1] = __shfl_down_sync(0xffffffffu, fv(0, a), 1);
 #pragma unroll
-      for (int v = 0; v < V - 1; ++v) out[v] = f[v + 1][a];
+      for (int v = 0; v < V - 1; ++v) out[v] = fv(v + 1, a);
       if (lane_ok && !last) VT::store(fb, a, N, d + col, out);
       if (last) {  // elements 0 .. V - 2
         if constexpr (V == 4) {
@@ -455,7 +484,7 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
           VT::store1(fb, a, N, d + col, out[0]);
         }
       }
-      if (first) VT::store1(fb, a, N, d + col_l, f[0][a]);
+      if (first) VT::store1(fb, a, N, d + col_l, fv(0, a));
     }
   }
 }
