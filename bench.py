@@ -33,23 +33,33 @@ def bytes_per_update(precision):
     return {"fp64": 144, "fp32_dev": 72, "fp16_dev": 40}[precision]
 
 
-def captured_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None when the
-    kernel source has changed since that capture."""
+# sources of the headline step kernel (step_vec_kernel, FP32 deviations); a profile summary
+# records their combined sha256 prefix, so its counters are only used for the code they measured
+KERNEL_SOURCES = ("step_vec.cu", "step_core.cuh", "d2q9.cuh")
+PROFILE_SUMMARY = "step_vec_kernel_fp32_dev_4096.md"
+
+
+def kernel_sources_sha():
     import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1908_09235_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic():
+    """DRAM bytes per launch of the headline step kernel from the committed ncu summary, or None
+    when the kernel's sources have changed since that capture."""
     import re
-    summary = os.path.join(ROOT, "profiles", "step_kernel_fp32_dev_4096.md")
-    src = os.path.join(ROOT, "paper_1908_09235_gb300", "csrc", "step.cu")
+    summary = os.path.join(ROOT, "profiles", PROFILE_SUMMARY)
     if not os.path.exists(summary):
         return None
     text = open(summary).read()
-    m_sha = re.search(r"step.cu sha256 prefix: ([0-9a-f]+)", text)
+    m_sha = re.search(r"kernel sources sha256 prefix: ([0-9a-f]+)", text)
     m_tr = re.search(r"traffic_bytes_per_launch: (\d+)", text)
-    if not (m_sha and m_tr):
+    if not (m_sha and m_tr) or m_sha.group(1) != kernel_sources_sha():
         return None
-    with open(src, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest()[:16] != m_sha.group(1):
-            return None
     return int(m_tr.group(1))
 
 
@@ -513,7 +523,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "step_kernel (fused force+collision+stream)",
+                         "kernel": "step_vec_kernel (fused force+collision+stream, "
+                                   "16-byte population vectors)",
                          "bytes_per_fluid_update": bpu},
             "step_kernel_us": round(1e3 * ms_step / args.steps, 2),
             "boundary_kernel_us": round(1e3 * ms_bnd / args.steps, 2),
