@@ -248,13 +248,15 @@ def run_e2e(w, steps):
 
 
 def run_profile_case(args):
-    """A single lattice of side L (cylinder 0.15 L, droplet 0.2 L) stepped a few times; used
-    as the small case of ncu captures."""
+    """A single lattice of side L stepped a few times (the benchmark's 4096^2 lattice, or one of
+    side L with cylinder 0.15 L and droplet 0.2 L); the case of ncu captures."""
     import torch
 
     from paper_1908_09235_gb300 import lbm, workloads
     L = args.profile_case
-    w = workloads.droplet_on_cylinder(L, 0.15 * L, 0.2 * L)
+    # 4096: the benchmark's own lattice; other sides: the same shape scaled
+    w = workloads.LARGE if L == workloads.LARGE.nx else workloads.droplet_on_cylinder(L, 0.15 * L,
+                                                                                      0.2 * L)
     lat, _ = make_lattice(w, lbm.SCHEMES[args.scheme], lbm.PRECISIONS[args.precision],
                           args.kernel_path)
     lat.step_timed(args.warmup)
