@@ -247,6 +247,66 @@ def run_e2e(w, steps):
     return info["n_fluid"] * steps / dt / 1e6, 24 * n / steps, 24 * n / steps
 
 
+def run_precision_report(args):
+    """The reduced-precision formats on long runs: FP32 and FP16 deviation storage (FP32
+    arithmetic, FP64 per-node mass bookkeeping in the wall pass, FP64 ledger) on droplet-on-
+    cylinder lattices of the given sides (the 4096^2 geometry scaled: cylinder 600/4096 L,
+    droplet 800/4096 L), scheme B.  Total-mass drift |m/m0 - 1| every --report-every steps; at
+    sides <= 2048 also the rho and u errors after the last step against the FP64 path on the same
+    lattice (the FP64 path is the oracle's stand-in here: the parity tests hold it to 1e-11 of
+    the CPU oracle, which would need hours for 20000 steps of 2048^2 on one core)."""
+    import numpy as np
+    import torch
+
+    from paper_1908_09235_gb300 import lbm, workloads
+    torch.cuda.set_device(0)
+    steps, every = args.report_steps, args.report_every
+    runs = []
+    for L in (int(v) for v in args.report_sides.split(",")):
+        w = workloads.droplet_on_cylinder(L, 600.0 / 4096 * L, 800.0 / 4096 * L)
+        ref = None
+        for pname in (("fp64",) if L <= 2048 else ()) + ("fp32_dev", "fp16_dev"):
+            lat, _ = make_lattice(w, lbm.MOD_B, lbm.PRECISIONS[pname])
+            m0 = lat.mass()
+            drift, done, status = [], 0, "ok"
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while done < steps:
+                n = min(every, steps - done)
+                lat.step(n)
+                done += n
+                try:
+                    drift.append(abs(lat.mass() / m0 - 1.0))
+                except lbm.LBMError as e:
+                    status = e.args[-1] if e.args else "unstable"
+                    break
+            wall = time.perf_counter() - t0
+            n_fluid = lat.info()["n_fluid"]
+            run = {"side": L, "storage": pname, "steps": done, "status": status,
+                   "mlups_incl_mass_reads": round(n_fluid * done / wall / 1e6, 1),
+                   "mass_drift_every_%d" % every: [float("%.3e" % d) for d in drift],
+                   "max_mass_drift": float("%.3e" % max(drift)) if drift else None}
+            if L <= 2048 and status == "ok":
+                rho, ux, uy = lat.fields()
+                if pname == "fp64":
+                    ref = (rho, ux, uy)
+                elif ref is not None:
+                    m = np.isfinite(ref[0])
+                    drho = np.abs(rho[m] - ref[0][m])
+                    du = np.maximum(np.abs(ux[m] - ref[1][m]), np.abs(uy[m] - ref[2][m]))
+                    umax = float(np.max(np.hypot(ref[1][m], ref[2][m])))
+                    run["vs_fp64"] = {
+                        "rho_max_abs": float("%.3e" % drho.max()),
+                        "rho_normwise": float("%.3e" % (drho.max() / np.max(ref[0][m]))),
+                        "rho_rms": float("%.3e" % np.sqrt(np.mean(drho ** 2))),
+                        "u_max_abs": float("%.3e" % du.max()),
+                        "u_max_ref": float("%.3e" % umax)}
+            lat.close()
+            runs.append(run)
+    print(json.dumps({"report": "reduced precision, droplet on cylinder, scheme B",
+                      "steps": steps, "runs": runs}), flush=True)
+
+
 def run_profile_case(args):
     """A single lattice of side L stepped a few times (the benchmark's 4096^2 lattice, or one of
     side L with cylinder 0.15 L and droplet 0.2 L); the case of ncu captures."""
@@ -295,10 +355,11 @@ def run_batched(args):
     info = b.info()
     b.step(args.warmup)
     torch.cuda.synchronize()
+    steps = args.batch_steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(0) as clk:
         e0.record()
-        b.step(args.steps)
+        b.step(steps)
         e1.record()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -310,7 +371,7 @@ def run_batched(args):
         except lbm.LBMError:
             unstable += 1
     b.close()
-    value = info["fluid_nodes"] * args.steps / (ms * 1e-3) / 1e6
+    value = info["fluid_nodes"] * steps / (ms * 1e-3) / 1e6
     # baseline: plain loop, one FP64 lattice at a time (first 16 lattices, 10 steps each)
     base_nodes, base_ms = 0, 0.0
     for w in ws[:16]:
@@ -326,8 +387,8 @@ def run_batched(args):
         lat.close()
     base = base_nodes / (base_ms * 1e-3) / 1e6
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "steps": steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec != lbm.FP64 else "f64", "data": "synthetic",
             "config": {"workload": "batched_droplets_%d" % len(ws), "storage": args.precision,
@@ -437,6 +498,13 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="the batched workload: many uneven lattices in one batch")
     ap.add_argument("--batch-domains", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=5000,
+                    help="batched workload: timed steps of every lattice")
+    ap.add_argument("--precision-report", action="store_true",
+                    help="FP32/FP16 deviation storage on long runs: mass drift and error vs FP64")
+    ap.add_argument("--report-sides", default="2048,8192")
+    ap.add_argument("--report-steps", type=int, default=20000)
+    ap.add_argument("--report-every", type=int, default=2000)
     ap.add_argument("--serve", action="store_true",
                     help="the served stream through the continuous-batching server")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -446,7 +514,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-chunk", type=int, default=200)
     ap.add_argument("--serve-hbm-gb", type=float, default=0.0,
-                    help="memory budget of the server (0: 80% of the free device memory)")
+                    help="memory budget of the server (0: 80%% of the free device memory)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -460,6 +528,8 @@ def main():
         return run_batched(args)
     if args.serve:
         return run_serve(args)
+    if args.precision_report:
+        return run_precision_report(args)
 
     import torch
     world, rank, local = dist_setup()
