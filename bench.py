@@ -247,6 +247,101 @@ def run_e2e(w, steps):
     return info["n_fluid"] * steps / dt / 1e6, 24 * n / steps, 24 * n / steps
 
 
+# Table 1 of the paper (Sec. 5.1): 2L/D, separation angle (degrees), drag coefficient
+TABLE1 = {20: {"scheme A": (1.90, 41.35, 2.130), "scheme B": (1.91, 41.56, 2.133),
+               "Dennis and Chang 1970": (1.88, 43.7, 2.045)},
+          40: {"scheme A": (4.61, 53.93, 1.590), "scheme B": (4.64, 53.93, 1.593),
+               "Dennis and Chang 1970": (4.69, 53.8, 1.522)}}
+
+
+def cylinder_wake(ux, uy, cx, cy, r, D):
+    """Wake length 2L/D (L from the cylinder's rearmost point to where u_x on the centre line
+    turns positive again) and separation angle (degrees from the rear stagnation point, where the
+    tangential velocity on a ring just outside the surface changes sign; mean of both halves)."""
+    import numpy as np
+    j = int(round(cy))
+    row = ux[j]
+    x_rear = cx + r
+    L = float("nan")
+    for i in range(int(np.ceil(x_rear)), row.size - 1):
+        if np.isfinite(row[i]) and np.isfinite(row[i + 1]) and row[i] < 0.0 <= row[i + 1]:
+            L = i + row[i] / (row[i] - row[i + 1]) - x_rear
+            break
+
+    def bilinear(a, x, y):
+        i0, j0 = int(np.floor(x)), int(np.floor(y))
+        tx, ty = x - i0, y - j0
+        return ((1 - tx) * (1 - ty) * a[j0, i0] + tx * (1 - ty) * a[j0, i0 + 1] +
+                (1 - tx) * ty * a[j0 + 1, i0] + tx * ty * a[j0 + 1, i0 + 1])
+
+    rs = r + 1.5
+    angles = []
+    for side in (1.0, -1.0):
+        prev = None
+        for k in range(1, 1800):
+            th = np.radians(0.1 * k)
+            x, y = cx + rs * np.cos(th), cy + side * rs * np.sin(th)
+            # tangential velocity towards the front, mirrored onto the upper half (u_y is odd
+            # under the reflection y -> 2 cy - y, u_x even)
+            ut = -np.sin(th) * bilinear(ux, x, y) + side * np.cos(th) * bilinear(uy, x, y)
+            if prev is not None and prev > 0.0 >= ut:
+                angles.append(0.1 * (k - 1) + 0.1 * prev / (prev - ut))
+                break
+            prev = ut
+    theta = float(np.mean(angles)) if angles else float("nan")
+    return 2.0 * L / D, theta
+
+
+def run_cylinder_flow(args):
+    """Steady flow past a circular cylinder, Sec. 5.1: domain 40 D x 25 D, cylinder of diameter
+    D at (15 D, 12.5 D), U0 = 0.1, Zou-He velocity inlet, fully developed outlet, periodic in y,
+    Re = U0 D / nu.  Runs each (Re, scheme) until the drag changes by less than 1e-6 (relative)
+    over 1000 steps, then reports C_d = F_x / (0.5 rho U0^2 D), 2L/D and the separation angle
+    beside Table 1 of the paper."""
+    import numpy as np
+    import torch
+
+    from paper_1908_09235_gb300 import lbm
+    torch.cuda.set_device(0)
+    D = args.cyl_diameter
+    nx, ny, U0 = 40 * D, 25 * D, 0.1
+    cx, cy, r = 15.0 * D, 12.5 * D, 0.5 * D
+    runs = []
+    for Re in (20, 40):
+        nu = U0 * D / Re
+        tau = 3.0 * nu + 0.5
+        for name in ("mod_a", "mod_b"):
+            lat = lbm.Lattice(nx, ny, tau, lbm.SCHEMES[name], circles=[(cx, cy, r)],
+                              eos=lbm.make_eos(lbm.EOS_NONE),
+                              precision=lbm.PRECISIONS[args.precision])
+            ux0 = np.full(nx * ny, U0)
+            lat.init_fields(np.ones(nx * ny), ux0, np.zeros(nx * ny))
+            lat.set_inflow(U0)
+            t0 = time.perf_counter()
+            cd_prev, steps, conv = None, 0, False
+            while steps < args.cyl_max_steps:
+                lat.step(1000)
+                steps += 1000
+                cd = lat.force()[0] / (0.5 * U0 * U0 * D)
+                if cd_prev is not None and abs(cd - cd_prev) < 1e-6 * abs(cd):
+                    conv = True
+                    break
+                cd_prev = cd
+            wall = time.perf_counter() - t0
+            rho, ux, uy = lat.fields()
+            n_fluid = lat.info()["n_fluid"]
+            lat.close()
+            wake, theta = cylinder_wake(ux, uy, cx, cy, r, D)
+            runs.append({"Re": Re, "scheme": name, "tau": round(tau, 4), "steps": steps,
+                         "converged": conv, "Cd": round(cd, 4), "2L/D": round(wake, 3),
+                         "theta_s_deg": round(theta, 2),
+                         "mlups": round(n_fluid * steps / wall / 1e6, 1),
+                         "table1": TABLE1[Re]})
+    print(json.dumps({"report": "steady flow past a circular cylinder (Sec. 5.1, Table 1)",
+                      "D": D, "domain": [nx, ny], "U0": U0, "storage": args.precision,
+                      "runs": runs}), flush=True)
+
+
 def run_precision_report(args):
     """The reduced-precision formats on long runs: FP32 and FP16 deviation storage (FP32
     arithmetic, FP64 per-node mass bookkeeping in the wall pass, FP64 ledger) on droplet-on-
@@ -500,6 +595,10 @@ def main():
     ap.add_argument("--batch-domains", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000,
                     help="batched workload: timed steps of every lattice")
+    ap.add_argument("--cylinder-flow", action="store_true",
+                    help="Sec. 5.1: flow past a cylinder at Re 20 and 40 against Table 1")
+    ap.add_argument("--cyl-diameter", type=int, default=40)
+    ap.add_argument("--cyl-max-steps", type=int, default=200000)
     ap.add_argument("--precision-report", action="store_true",
                     help="FP32/FP16 deviation storage on long runs: mass drift and error vs FP64")
     ap.add_argument("--report-sides", default="2048,8192")
@@ -530,6 +629,8 @@ def main():
         return run_serve(args)
     if args.precision_report:
         return run_precision_report(args)
+    if args.cylinder_flow:
+        return run_cylinder_flow(args)
 
     import torch
     world, rank, local = dist_setup()

@@ -197,6 +197,23 @@ lbm_status lbm_links(lbm_ctx* ctx, int32_t* node, uint8_t* dir, double* q, int64
 
 lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
 
+/* Channel flow past solid bodies (Sec. 5.1, steady flow past a circular cylinder): from the next
+ * step on, column i = 0 is a velocity inlet with the uniform profile (u_in, 0) imposed by Zou and
+ * He's rule for the three populations entering from the left, and column i = nx - 1 is a
+ * fully developed outlet (the three populations entering from the right are those of column
+ * nx - 2).  y stays periodic.  Single-phase flows only (eos kind LBM_EOS_NONE: the psi stencil is
+ * not defined at an open end); |u_in| < 0.5; nx >= 3.  Takes effect for lbm_step, lbm_step_timed
+ * and later graphs; there is no call to return to a periodic x. */
+lbm_status lbm_set_inflow(lbm_ctx* ctx, double u_in);
+
+/* Force on all solid nodes during the last time step by momentum exchange (Sec. 5.1, after Mei
+ * et al. 2002): the sum over cut links of e_a (f*_a(x_b, t) + f_abar(x_b, t+1)), the incoming
+ * value being the one the curved-wall scheme wrote, in lattice units (momentum per step).
+ * FP64, per boundary node in a fixed lane order, then over boundary nodes in ascending order on
+ * the host.  Blocks.  0 before the first step and when there are no cut links.  The drag
+ * coefficient of Sec. 5.1 is fx / (0.5 rho U0^2 D). */
+lbm_status lbm_force(lbm_ctx* ctx, double* fx, double* fy);
+
 /* Total mass of caller-owned device arrays without allocating any memory.  (This entry point
  * has no counterpart in the paper; it serves callers that cannot allocate device memory: a host
  * framework that already holds the device memory in its own pool, or a latency-critical loop

@@ -97,6 +97,8 @@ def _load():
             "or_last_leak": (C.c_double, [_P]),
             "or_last_max_node_leak": (C.c_double, [_P]),
             "or_fallbacks": (C.c_long, [_P]),
+            "or_set_inflow": (None, [_P, C.c_double]),
+            "or_force": (None, [_P, _D, _D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -262,3 +264,14 @@ class OracleSim:
     @property
     def fallbacks(self):
         return self._lib.or_fallbacks(self._s)
+
+    def set_inflow(self, u_in):
+        """Channel mode (Sec. 5.1): Zou-He velocity inlet at i = 0, fully developed outlet at
+        i = nx - 1; single-phase flows."""
+        self._lib.or_set_inflow(self._s, float(u_in))
+
+    def force(self):
+        """Momentum-exchange force (fx, fy) on the solid nodes during the last step."""
+        fx, fy = C.c_double(), C.c_double()
+        self._lib.or_force(self._s, C.byref(fx), C.byref(fy))
+        return fx.value, fy.value

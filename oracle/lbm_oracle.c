@@ -41,6 +41,11 @@ struct or_sim {
   double* lq;
   long fallbacks;
   double last_leak, last_max_node_leak;
+  /* channel mode (flow past a cylinder, Sec. 5.1): velocity inlet at i = 0, outlet at nx - 1 */
+  int open_x;
+  double u_in;
+  /* momentum-exchange force on the solid nodes during the last step */
+  double force_x, force_y;
 };
 
 /* ------------------------------------------------------------------------------------------ */
@@ -470,7 +475,7 @@ static double ghost_bracket(int a, double usx, double usy, double ubx, double ub
 static void apply_boundary(or_sim* s) {
   size_t N = (size_t)s->N;
   int nx = s->nx, ny = s->ny, scheme = s->p.scheme;
-  double leak = 0.0, maxleak = 0.0;
+  double leak = 0.0, maxleak = 0.0, force_x = 0.0, force_y = 0.0;
   for (int b = 0; b < s->nb; ++b) {
     int n = s->bnode[b];
     int i = n % nx, j = n / nx;
@@ -496,6 +501,7 @@ static void apply_boundary(or_sim* s) {
       if (den != 0.0) rho_s = num / den; /* den = 0 only when every chi = 0: rho_s then unused */
     }
     double sum_out = 0.0, sum_in = 0.0;
+    double node_fx = 0.0, node_fy = 0.0;
     for (int l = l0; l < l1; ++l) {
       int a = s->ldir[l], ab = OPP[a];
       double q = s->lq[l];
@@ -561,7 +567,14 @@ static void apply_boundary(or_sim* s) {
       s->fn[ab * N + n] = val;
       sum_out += fo;
       sum_in += val;
+      /* Momentum exchange (Sec. 5.1, after Mei et al. 2002): f*_a(x_b) goes into the wall
+       * along e_a and f_abar(x_b, t+1) comes back along -e_a, so the wall receives
+       * e_a (f*_a + f_abar) through this link. */
+      node_fx += EX[a] * (fo + val);
+      node_fy += EY[a] * (fo + val);
     }
+    force_x += node_fx;
+    force_y += node_fy;
     double dm = sum_out - sum_in; /* Eq. (15) */
     leak += dm;
     if (scheme == OR_MOD_A || scheme == OR_BOUZIDI_L_A) {
@@ -572,6 +585,38 @@ static void apply_boundary(or_sim* s) {
   }
   s->last_leak = leak;
   s->last_max_node_leak = maxleak;
+  s->force_x = force_x;
+  s->force_y = force_y;
+}
+
+/* Channel ends (Sec. 5.1), after streaming and the wall schemes.  Inlet i = 0: the populations
+ * entering from the left (1, 5, 8) follow from the prescribed velocity (u_in, 0) and the known
+ * ones by Zou and He's rule (bounce-back of the non-equilibrium part normal to the inlet):
+ *   rho = (f0 + f2 + f4 + 2 (f3 + f6 + f7)) / (1 - u_in)
+ *   f1 = f3 + 2/3 rho u_in,  f5 = f7 - (f2 - f4)/2 + rho u_in/6,  f8 = f6 + (f2 - f4)/2 + rho u_in/6.
+ * Outlet i = nx - 1, fully developed flow: the populations entering from the right (3, 6, 7)
+ * equal those of column nx - 2. */
+static void apply_open_x(or_sim* s) {
+  size_t N = (size_t)s->N;
+  int nx = s->nx, ny = s->ny;
+  double u = s->u_in;
+  for (int j = 0; j < ny; ++j) {
+    int n = j * nx;
+    if (!s->solid[n]) {
+      double* f = s->fn;
+      double f0 = f[0 * N + n], f2 = f[2 * N + n], f3 = f[3 * N + n], f4 = f[4 * N + n];
+      double f6 = f[6 * N + n], f7 = f[7 * N + n];
+      double rho = (f0 + f2 + f4 + 2.0 * (f3 + f6 + f7)) / (1.0 - u);
+      f[1 * N + n] = f3 + 2.0 / 3.0 * rho * u;
+      f[5 * N + n] = f7 - 0.5 * (f2 - f4) + rho * u / 6.0;
+      f[8 * N + n] = f6 + 0.5 * (f2 - f4) + rho * u / 6.0;
+    }
+    int m = j * nx + nx - 1;
+    if (!s->solid[m]) {
+      const int in_dirs[3] = {3, 6, 7};
+      for (int k = 0; k < 3; ++k) s->fn[in_dirs[k] * N + m] = s->fn[in_dirs[k] * N + m - 1];
+    }
+  }
 }
 
 void or_step(or_sim* s, int nsteps) {
@@ -603,6 +648,7 @@ void or_step(or_sim* s, int nsteps) {
         }
       }
     apply_boundary(s);
+    if (s->open_x) apply_open_x(s);
     double* t = s->f;
     s->f = s->fn;
     s->fn = t;
@@ -638,5 +684,13 @@ void or_fields(or_sim* s, double* rho, double* ux, double* uy) {
 void or_get_f(const or_sim* s, double* f) { memcpy(f, s->f, sizeof(double) * 9 * (size_t)s->N); }
 void or_set_f(or_sim* s, const double* f) { memcpy(s->f, f, sizeof(double) * 9 * (size_t)s->N); }
 double or_last_leak(const or_sim* s) { return s->last_leak; }
+void or_set_inflow(or_sim* s, double u_in) {
+  s->open_x = 1;
+  s->u_in = u_in;
+}
+void or_force(const or_sim* s, double* fx, double* fy) {
+  *fx = s->force_x;
+  *fy = s->force_y;
+}
 double or_last_max_node_leak(const or_sim* s) { return s->last_max_node_leak; }
 long or_fallbacks(const or_sim* s) { return s->fallbacks; }

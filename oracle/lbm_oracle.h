@@ -86,6 +86,13 @@ void or_set_f(or_sim* s, const double* f);
 double or_last_leak(const or_sim* s);   /* sum over boundary nodes of Eq. (15) in the last step */
 double or_last_max_node_leak(const or_sim* s); /* max |Eq. (15)| after any correction */
 long or_fallbacks(const or_sim* s);
+/* Channel mode for the flow past a cylinder (Sec. 5.1): Zou-He velocity inlet (u_in, 0) at
+ * i = 0 and a fully developed outlet at i = nx - 1 (x no longer periodic; y stays periodic).
+ * Single-phase flows only (the psi stencil would still wrap in x). */
+void or_set_inflow(or_sim* s, double u_in);
+/* Momentum-exchange force on all solid nodes during the last step: the sum over cut links of
+ * e_a (f*_a(x_b, t) + f_abar(x_b, t+1)), lattice units. */
+void or_force(const or_sim* s, double* fx, double* fy);
 
 #ifdef __cplusplus
 }

@@ -189,7 +189,8 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
                                                const double* __restrict__ rho_m,
                                                const double* __restrict__ ux_m,
                                                const double* __restrict__ uy_m,
-                                               double* __restrict__ carry, unsigned mask) {
+                                               double* __restrict__ carry,
+                                               double* __restrict__ force, unsigned mask) {
   using T = typename Pop<S>::C;
   constexpr bool DEV = Pop<S>::dev;
   const int scheme = p.scheme;
@@ -277,6 +278,18 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
     const bool copy = DEV && !gh && x1 < 0 && x2 < 0 && c0 == T(1);
     in_d = Pop<S>::store_t(L.dst, dst, N, copy ? fo_d : val - wr);
   }
+  if (force) {
+    // Momentum exchange (Sec. 5.1, after Mei et al. 2002): through link a the wall receives
+    // e_a (f*_a(x_b, t) + f_abar(x_b, t+1)), with the incoming value as stored; FP64 sums over
+    // the node's links in the fixed group order, one (fx, fy) per boundary node.
+    const double m = act ? double(fo_d) + double(in_d) + 2.0 * wgt<double>(a) * L.rho_ref : 0.0;
+    const double fx = group8_sum(double(ex(a)) * m, mask);
+    const double fy = group8_sum(double(ey(a)) * m, mask);
+    if (lane0) {
+      force[2 * b] = fx;
+      force[2 * b + 1] = fy;
+    }
+  }
 
   if constexpr (DEV) {
     if (conserving) {
@@ -309,11 +322,46 @@ __global__ void __launch_bounds__(128) boundary_kernel(DevParams p, int nb,
                                                        const double* __restrict__ rho_m,
                                                        const double* __restrict__ ux_m,
                                                        const double* __restrict__ uy_m,
-                                                       double* __restrict__ carry) {
+                                                       double* __restrict__ carry,
+                                                       double* __restrict__ force) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = gt >> 3;
   boundary_group<S>(p, b, gt & 7, b < nb, bnode, boff, ldir, r, L, rho_m, ux_m, uy_m, carry,
-                    0xffffffffu);
+                    force, 0xffffffffu);
+}
+
+// Channel ends (Sec. 5.1), after streaming and the wall pass; one thread per row j.  Inlet
+// i = 0: the populations entering from the left (1, 5, 8) follow from the prescribed velocity
+// (u_in, 0) and the known ones by Zou and He's rule:
+//   rho = (f0 + f2 + f4 + 2 (f3 + f6 + f7)) / (1 - u_in),  f1 = f3 + 2/3 rho u_in,
+//   f5 = f7 - (f2 - f4)/2 + rho u_in / 6,  f8 = f6 + (f2 - f4)/2 + rho u_in / 6.
+// Outlet i = nx - 1 (fully developed flow): the populations entering from the right (3, 6, 7)
+// equal those of column nx - 2.  FP64 arithmetic on the full populations (deviation + w rho_ref).
+template <typename S>
+__global__ void open_x_kernel(DevParams p, void* __restrict__ fb,
+                              const uint8_t* __restrict__ flags, double u_in) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p.ny) return;
+  const int nx = p.nx, N = p.N;
+  const double rr = p.rho_ref;
+  auto get = [&](int a, int n) { return Pop<S>::load_e(fb, a * N + n, N) + wgt<double>(a) * rr; };
+  auto put = [&](int a, int n, double v) { Pop<S>::store_e(fb, a * N + n, N, v - wgt<double>(a) * rr); };
+  const int n0 = j * nx;
+  if (!(flags[n0] & FLAG_SOLID)) {
+    const double f0 = get(0, n0), f2 = get(2, n0), f3 = get(3, n0), f4 = get(4, n0);
+    const double f6 = get(6, n0), f7 = get(7, n0);
+    const double rho = (f0 + f2 + f4 + 2.0 * (f3 + f6 + f7)) / (1.0 - u_in);
+    put(1, n0, f3 + 2.0 / 3.0 * rho * u_in);
+    put(5, n0, f7 - 0.5 * (f2 - f4) + rho * u_in / 6.0);
+    put(8, n0, f6 + 0.5 * (f2 - f4) + rho * u_in / 6.0);
+  }
+  const int n1 = j * nx + nx - 1;
+  if (!(flags[n1] & FLAG_SOLID)) {
+    // copies of stored values: no rounding for any format
+    Pop<S>::store_e(fb, 3 * N + n1, N, Pop<S>::load_e(fb, 3 * N + n1 - 1, N));
+    Pop<S>::store_e(fb, 6 * N + n1, N, Pop<S>::load_e(fb, 6 * N + n1 - 1, N));
+    Pop<S>::store_e(fb, 7 * N + n1, N, Pop<S>::load_e(fb, 7 * N + n1 - 1, N));
+  }
 }
 
 // Boundary nodes of many lattices: items are (domain, boundary node); a persistent grid of
@@ -333,7 +381,7 @@ __global__ void __launch_bounds__(128) batch_boundary_kernel(const BatchDomain* 
     const int cur = D.cur;
     const Lat<S> L{D.f[cur], D.f[cur ^ 1], D.p.N, D.p.rho_ref};
     boundary_group<S>(D.p, it.y, k, true, D.bnode, D.boff, D.ldir, D.recipe, L, D.rho_m, D.ux_m,
-                      D.uy_m, D.carry, mask);
+                      D.uy_m, D.carry, nullptr, mask);
   }
 }
 
@@ -350,11 +398,11 @@ template <typename S>
 cudaError_t launch_b(const DevParams& p, int nb, const int32_t* bnode, const int32_t* boff,
                      const uint8_t* ldir, LinkRecipe r, const void* fa, void* fb,
                      const double* rho_m, const double* ux_m, const double* uy_m, double* carry,
-                     cudaStream_t s) {
+                     double* force, cudaStream_t s) {
   Lat<S> L{fa, fb, p.N, p.rho_ref};  // rho_ref also in p.k<T>() for the FP32 formats
   const long long threads = 8LL * nb;
   boundary_kernel<S><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
-      p, nb, bnode, boff, ldir, r, L, rho_m, ux_m, uy_m, carry);
+      p, nb, bnode, boff, ldir, r, L, rho_m, ux_m, uy_m, carry, force);
   return cudaGetLastError();
 }
 
@@ -419,13 +467,26 @@ cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, cudaStream_t s) 
 cudaError_t launch_boundary(int precision, const DevParams& p, int nb, const int32_t* bnode,
                             const int32_t* boff, const uint8_t* ldir, LinkRecipe r,
                             const void* fa, void* fb, const double* rho_m, const double* ux_m,
-                            const double* uy_m, double* carry, cudaStream_t s) {
+                            const double* uy_m, double* carry, double* force, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   if (precision == LBM_FP32_DEV)
-    return launch_b<float>(p, nb, bnode, boff, ldir, r, fa, fb, rho_m, ux_m, uy_m, carry, s);
+    return launch_b<float>(p, nb, bnode, boff, ldir, r, fa, fb, rho_m, ux_m, uy_m, carry, force, s);
   if (precision == LBM_FP16_DEV)
-    return launch_b<__half>(p, nb, bnode, boff, ldir, r, fa, fb, rho_m, ux_m, uy_m, carry, s);
-  return launch_b<double>(p, nb, bnode, boff, ldir, r, fa, fb, rho_m, ux_m, uy_m, carry, s);
+    return launch_b<__half>(p, nb, bnode, boff, ldir, r, fa, fb, rho_m, ux_m, uy_m, carry, force,
+                            s);
+  return launch_b<double>(p, nb, bnode, boff, ldir, r, fa, fb, rho_m, ux_m, uy_m, carry, force, s);
+}
+
+cudaError_t launch_open_x(int precision, const DevParams& p, void* fb, const uint8_t* flags,
+                          double u_in, cudaStream_t s) {
+  const unsigned grid = (unsigned)((p.ny + 127) / 128);
+  if (precision == LBM_FP32_DEV)
+    open_x_kernel<float><<<grid, 128, 0, s>>>(p, fb, flags, u_in);
+  else if (precision == LBM_FP16_DEV)
+    open_x_kernel<__half><<<grid, 128, 0, s>>>(p, fb, flags, u_in);
+  else
+    open_x_kernel<double><<<grid, 128, 0, s>>>(p, fb, flags, u_in);
+  return cudaGetLastError();
 }
 
 }  // namespace lbm

@@ -93,8 +93,12 @@ lbm_status launch_one_step(lbm_ctx* c, cudaStream_t s, int cur) {
   cudaError_t e = launch_bulk(c, s, cur);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
   e = launch_boundary(c->precision, c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->recipe, fa,
-                      fb, c->rho_m, c->ux_m, c->uy_m, c->carry, s);
+                      fb, c->rho_m, c->ux_m, c->uy_m, c->carry, c->force, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "boundary kernel launch");
+  if (c->open_x) {
+    e = launch_open_x(c->precision, c->p, fb, c->flags, c->u_in, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "channel-end kernel launch");
+  }
   return LBM_OK;
 }
 
@@ -305,7 +309,8 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
   // ---- second allocation: boundary-link CSR and the FP64 rounding carry ----
   if (c->nb > 0) {
     size_t b2 = align_up(c->nb * 4) + align_up((c->nb + 1) * 4) + align_up(c->nl) +
-                align_up(c->nl * 8) + align_up(c->nb * 8) + align_up(link_recipe_bytes(c->nl));
+                align_up(c->nl * 8) + align_up(c->nb * 8) + align_up(c->nb * 16) +
+                align_up(link_recipe_bytes(c->nl));
     void* base2 = dev_alloc(c, b2);
     if (!base2) {
       release_all(c);
@@ -318,6 +323,7 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
     c->ldir = c2.take<uint8_t>(c->nl);
     c->lq = c2.take<double>(c->nl);
     c->carry = c2.take<double>(c->nb);
+    c->force = c2.take<double>(2 * c->nb);
     link_recipe_carve(c2.take<char>(link_recipe_bytes(c->nl)), c->nl, &c->recipe);
     if ((e = launch_geom_emit(g, c->flags, c->geom_tmp, c->bnode, c->boff, c->ldir, c->lq,
                               c->stream)) != cudaSuccess)
@@ -328,6 +334,8 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
       return bail(e, "copy boff");
     if ((e = cudaMemsetAsync(c->carry, 0, c->nb * 8, c->stream)) != cudaSuccess)
       return bail(e, "memset carry");
+    if ((e = cudaMemsetAsync(c->force, 0, c->nb * 16, c->stream)) != cudaSuccess)
+      return bail(e, "memset force");
     if ((e = launch_link_setup(c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->lq, c->flags,
                                c->recipe, c->stream)) != cudaSuccess)
       return bail(e, "link setup");
@@ -457,8 +465,12 @@ lbm_status lbm_step_timed(lbm_ctx* c, int32_t n, double* ms_step, double* ms_bnd
     if (st == LBM_OK) {
       e = launch_boundary(c->precision, c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->recipe,
                           c->f[cur], c->f[1 - cur], c->rho_m, c->ux_m, c->uy_m, c->carry,
-                          c->stream);
+                          c->force, c->stream);
       if (e != cudaSuccess) st = cuda_fail(c, e, "boundary kernel launch");
+    }
+    if (st == LBM_OK && c->open_x) {
+      e = launch_open_x(c->precision, c->p, c->f[1 - cur], c->flags, c->u_in, c->stream);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "channel-end kernel launch");
     }
     if (st == LBM_OK) cudaEventRecord(ev[2 * k + 2], c->stream);
     c->cur = 1 - cur;
@@ -575,6 +587,43 @@ lbm_status lbm_info(lbm_ctx* c, lbm_info_t* o) {
   o->fallbacks = 0;
   o->T = c->T;
   o->psi_wall = c->p.psi_wall;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_inflow(lbm_ctx* c, double u_in) {
+  if (!c) return LBM_EINVAL;
+  if (c->status) return c->status;
+  if (!std::isfinite(u_in) || std::fabs(u_in) >= 0.5)
+    return fail(c, LBM_EINVAL, "inflow velocity must be finite and below 0.5 in lattice units");
+  if (c->p.eos != LBM_EOS_NONE)
+    return fail(c, LBM_EINVAL, "channel ends are for single-phase flows (eos kind NONE)");
+  if (c->p.nx < 3) return fail(c, LBM_EINVAL, "a channel needs nx >= 3");
+  for (int k = 0; k < 2; ++k)  // the captured steps do not contain the channel-end pass
+    if (c->graph[k]) {
+      cudaGraphExecDestroy(c->graph[k]);
+      c->graph[k] = nullptr;
+    }
+  c->open_x = true;
+  c->u_in = u_in;
+  return LBM_OK;
+}
+
+lbm_status lbm_force(lbm_ctx* c, double* fx, double* fy) {
+  if (!c || !fx || !fy) return LBM_EINVAL;
+  if (c->status) return c->status;
+  double sx = 0.0, sy = 0.0;
+  if (c->nb > 0) {
+    std::vector<double> h(2 * c->nb);
+    LBM_CUDA(c, cudaMemcpyAsync(h.data(), c->force, c->nb * 16, cudaMemcpyDeviceToHost,
+                                c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (long long b = 0; b < c->nb; ++b) {  // boundary nodes in ascending order
+      sx += h[2 * b];
+      sy += h[2 * b + 1];
+    }
+  }
+  *fx = sx;
+  *fy = sy;
   return LBM_OK;
 }
 

@@ -144,7 +144,11 @@ cudaError_t launch_link_setup(const DevParams& p, int nb, const int32_t* bnode,
 cudaError_t launch_boundary(int precision, const DevParams& p, int nb, const int32_t* bnode,
                             const int32_t* boff, const uint8_t* ldir, LinkRecipe r,
                             const void* fa, void* fb, const double* rho_m, const double* ux_m,
-                            const double* uy_m, double* carry, cudaStream_t s);
+                            const double* uy_m, double* carry, double* force, cudaStream_t s);
+// force: per boundary node (fx, fy) of the momentum exchange with the walls, or nullptr
+// Channel ends (velocity inlet at column 0, fully developed outlet at column nx - 1)
+cudaError_t launch_open_x(int precision, const DevParams& p, void* fb, const uint8_t* flags,
+                          double u_in, cudaStream_t s);
 
 // batched kernels (step.cu, boundary.cu, batch.cu)
 int batch_tile_rows(int ry);
@@ -207,6 +211,9 @@ struct lbm_ctx {
   uint8_t* ldir = nullptr;
   double* lq = nullptr;
   double* carry = nullptr;
+  double* force = nullptr;    // per boundary node (fx, fy) of the last step's momentum exchange
+  bool open_x = false;        // channel mode (lbm_set_inflow)
+  double u_in = 0.0;
   lbm::LinkRecipe recipe{};
   double* partials = nullptr;
   double* mass_out = nullptr;

@@ -32,7 +32,8 @@ EXPORTS = ("lbm_create", "lbm_coexistence", "lbm_init_fields", "lbm_init_droplet
            "lbm_mass_noalloc", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
            "lbm_batch_set_steps", "lbm_batch_step", "lbm_batch_step_timed", "lbm_batch_progress",
            "lbm_batch_domain", "lbm_batch_tune", "lbm_batch_info", "lbm_domain_bytes",
-           "lbm_batch_last_error", "lbm_batch_destroy", "lbm_batch_poll")
+           "lbm_batch_last_error", "lbm_batch_destroy", "lbm_batch_poll", "lbm_set_inflow",
+           "lbm_force")
 
 
 class LBMError(RuntimeError):
@@ -143,6 +144,8 @@ def load_library(build_if_missing=True):
             "lbm_batch_last_error": (C.c_char_p, [P]),
             "lbm_batch_destroy": (None, [P]),
             "lbm_batch_poll": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int64)]),
+            "lbm_set_inflow": (C.c_int, [P, C.c_double]),
+            "lbm_force": (C.c_int, [P, D, D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -228,6 +231,16 @@ def lbm_mass(ctx):
     m = C.c_double()
     _check(ctx, load_library().lbm_mass(ctx, C.byref(m)))
     return m.value
+
+
+def lbm_set_inflow(ctx, u_in):
+    _check(ctx, load_library().lbm_set_inflow(ctx, float(u_in)))
+
+
+def lbm_force(ctx):
+    fx, fy = C.c_double(), C.c_double()
+    _check(ctx, load_library().lbm_force(ctx, C.byref(fx), C.byref(fy)))
+    return fx.value, fy.value
 
 
 def lbm_info(ctx):
@@ -365,6 +378,14 @@ class Lattice:
 
     def info(self):
         return lbm_info(self.ctx)
+
+    def set_inflow(self, u_in):
+        """Channel mode (Sec. 5.1): velocity inlet (u_in, 0) at x = 0, fully developed outlet."""
+        lbm_set_inflow(self.ctx, u_in)
+
+    def force(self):
+        """Momentum-exchange force (fx, fy) on the solid nodes during the last step."""
+        return lbm_force(self.ctx)
 
 
 # ---- batches -------------------------------------------------------------------------------------
