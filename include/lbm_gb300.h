@@ -129,7 +129,9 @@ typedef struct {
                         *    persistent kernel that stages tiles by TMA; otherwise as 0;         *
                         * 3: the vectorised kernel wherever nx % 4 == 0 (FP64: nx % 2 == 0) and *
                         *    ny >= 8, FP64 included; otherwise the scalar tile kernel            */
-  int32_t pad;
+  int32_t track_force; /* nonzero: the wall pass records the momentum exchange for lbm_force   *
+                        * (also switched on by lbm_set_inflow); off by default, it costs the   *
+                        * wall pass a few microseconds per step; ignored by batches            */
 } lbm_options;
 
 typedef struct {
@@ -198,7 +200,7 @@ lbm_status lbm_links(lbm_ctx* ctx, int32_t* node, uint8_t* dir, double* q, int64
 lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
 
 /* Channel flow past solid bodies (Sec. 5.1, steady flow past a circular cylinder): from the next
- * step on, column i = 0 is a velocity inlet with the uniform profile (u_in, 0) imposed by Zou and
+ * step on (and with the force recorded for lbm_force), column i = 0 is a velocity inlet with the uniform profile (u_in, 0) imposed by Zou and
  * He's rule for the three populations entering from the left, and column i = nx - 1 is a
  * fully developed outlet (the three populations entering from the right are those of column
  * nx - 2).  y stays periodic.  Single-phase flows only (eos kind LBM_EOS_NONE: the psi stencil is
@@ -210,8 +212,9 @@ lbm_status lbm_set_inflow(lbm_ctx* ctx, double u_in);
  * et al. 2002): the sum over cut links of e_a (f*_a(x_b, t) + f_abar(x_b, t+1)), the incoming
  * value being the one the curved-wall scheme wrote, in lattice units (momentum per step).
  * FP64, per boundary node in a fixed lane order, then over boundary nodes in ascending order on
- * the host.  Blocks.  0 before the first step and when there are no cut links.  The drag
- * coefficient of Sec. 5.1 is fx / (0.5 rho U0^2 D). */
+ * the host.  Blocks.  0 before the first recorded step and when there are no cut links.
+ * LBM_ESTATE unless the context records the force (lbm_options.track_force or
+ * lbm_set_inflow).  The drag coefficient of Sec. 5.1 is fx / (0.5 rho U0^2 D). */
 lbm_status lbm_force(lbm_ctx* ctx, double* fx, double* fy);
 
 /* Total mass of caller-owned device arrays without allocating any memory.  (This entry point

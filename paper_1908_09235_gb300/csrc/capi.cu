@@ -93,7 +93,8 @@ lbm_status launch_one_step(lbm_ctx* c, cudaStream_t s, int cur) {
   cudaError_t e = launch_bulk(c, s, cur);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
   e = launch_boundary(c->precision, c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->recipe, fa,
-                      fb, c->rho_m, c->ux_m, c->uy_m, c->carry, c->force, s);
+                      fb, c->rho_m, c->ux_m, c->uy_m, c->carry,
+                      c->track_force ? c->force : nullptr, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "boundary kernel launch");
   if (c->open_x) {
     e = launch_open_x(c->precision, c->p, fb, c->flags, c->u_in, s);
@@ -354,6 +355,7 @@ lbm_status lbm_create(const lbm_geometry* geo, const lbm_eos* eos, double tau, i
   if ((e = cudaMemsetAsync(c->f[1], 0, c->lattice_bytes, c->stream)) != cudaSuccess)
     return bail(e, "memset f1");
   c->kernel_path = opt ? opt->kernel_path : 0;
+  c->track_force = opt && opt->track_force != 0;
   if (opt && opt->kernel_path == 2 && tma_step_supported(precision, geo->nx, geo->ny))
     c->use_tma = make_lattice_tensor_map(c->tmap[0], c->f[0], geo->nx, geo->ny) &&
                  make_lattice_tensor_map(c->tmap[1], c->f[1], geo->nx, geo->ny) &&
@@ -465,7 +467,7 @@ lbm_status lbm_step_timed(lbm_ctx* c, int32_t n, double* ms_step, double* ms_bnd
     if (st == LBM_OK) {
       e = launch_boundary(c->precision, c->p, (int)c->nb, c->bnode, c->boff, c->ldir, c->recipe,
                           c->f[cur], c->f[1 - cur], c->rho_m, c->ux_m, c->uy_m, c->carry,
-                          c->force, c->stream);
+                          c->track_force ? c->force : nullptr, c->stream);
       if (e != cudaSuccess) st = cuda_fail(c, e, "boundary kernel launch");
     }
     if (st == LBM_OK && c->open_x) {
@@ -605,12 +607,15 @@ lbm_status lbm_set_inflow(lbm_ctx* c, double u_in) {
     }
   c->open_x = true;
   c->u_in = u_in;
+  c->track_force = true;
   return LBM_OK;
 }
 
 lbm_status lbm_force(lbm_ctx* c, double* fx, double* fy) {
   if (!c || !fx || !fy) return LBM_EINVAL;
   if (c->status) return c->status;
+  if (!c->track_force)
+    return fail(c, LBM_ESTATE, "the force is not recorded (lbm_options.track_force)");
   double sx = 0.0, sy = 0.0;
   if (c->nb > 0) {
     std::vector<double> h(2 * c->nb);

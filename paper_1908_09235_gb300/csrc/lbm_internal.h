@@ -212,6 +212,7 @@ struct lbm_ctx {
   double* lq = nullptr;
   double* carry = nullptr;
   double* force = nullptr;    // per boundary node (fx, fy) of the last step's momentum exchange
+  bool track_force = false;   // the wall pass fills `force` (lbm_options.track_force, inflow)
   bool open_x = false;        // channel mode (lbm_set_inflow)
   double u_in = 0.0;
   lbm::LinkRecipe recipe{};

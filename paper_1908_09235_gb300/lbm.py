@@ -68,7 +68,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("graph_steps", C.c_int32), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("rho_ref", C.c_double), ("kernel_path", C.c_int32), ("pad", C.c_int32)]
+                ("rho_ref", C.c_double), ("kernel_path", C.c_int32), ("track_force", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -314,7 +314,7 @@ class Lattice:
 
     def __init__(self, nx, ny, tau, scheme=HBB, circles=(), wall_q_lo=0.0, wall_q_hi=0.0,
                  eos=None, precision=FP64, stream=None, torch_memory=True, graph_steps=0,
-                 rho_ref=0.0, kernel_path=0):
+                 rho_ref=0.0, kernel_path=0, track_force=False):
         self.nx, self.ny = int(nx), int(ny)
         if isinstance(scheme, str):
             scheme = SCHEMES[scheme]
@@ -329,6 +329,7 @@ class Lattice:
         opt.graph_steps = int(graph_steps)
         opt.rho_ref = float(rho_ref)
         opt.kernel_path = int(kernel_path)
+        opt.track_force = int(bool(track_force))
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream

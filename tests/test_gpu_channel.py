@@ -16,7 +16,7 @@ TAU, U_IN = 0.8, 0.05
 
 def _gpu(scheme, precision, path=0, steps=400, inflow=True):
     lat = lbm.Lattice(NX, NY, TAU, scheme, circles=[CYL], eos=lbm.make_eos(lbm.EOS_NONE),
-                      precision=precision, kernel_path=path)
+                      precision=precision, kernel_path=path, track_force=not inflow)
     lat.init_fields(np.ones(NX * NY))
     if inflow:
         lat.set_inflow(U_IN)
@@ -71,6 +71,17 @@ def test_channel_vector_kernel_equals_scalar_tiles(gpu_lib, precision):
 def test_force_at_rest_is_zero(gpu_lib):
     _, (fx, fy), _ = _gpu(lbm.MOD_B, lbm.FP64, steps=20, inflow=False)
     assert abs(fx) < 1e-13 and abs(fy) < 1e-13
+
+
+def test_force_needs_recording(gpu_lib):
+    lat = lbm.Lattice(64, 32, 1.0, lbm.MOD_B, circles=[(20.0, 16.0, 5.0)],
+                      eos=lbm.make_eos(lbm.EOS_NONE))
+    lat.init_fields(np.ones(64 * 32))
+    lat.step(2)
+    with pytest.raises(lbm.LBMError) as e:
+        lat.force()
+    assert e.value.status == 6  # LBM_ESTATE
+    lat.close()
 
 
 def test_inflow_rejects_two_phase_and_bad_velocity(gpu_lib):
