@@ -121,6 +121,7 @@ lbm_status build_graph(lbm_ctx* c, int parity) {
   e = cudaGraphInstantiate(&c->graph[parity], graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  c->graph_rho_ref = c->p.rho_ref;
   return LBM_OK;
 }
 
@@ -371,11 +372,13 @@ void lbm_destroy(lbm_ctx* c) {
 }
 
 static lbm_status init_common(lbm_ctx* c) {
-  for (int k = 0; k < 2; ++k)  // kernel parameters (rho_ref) may have changed
-    if (c->graph[k]) {
-      cudaGraphExecDestroy(c->graph[k]);
-      c->graph[k] = nullptr;
-    }
+  // captured steps hold the kernel parameters by value: keep them while rho_ref is unchanged
+  if (c->p.rho_ref != c->graph_rho_ref)
+    for (int k = 0; k < 2; ++k)
+      if (c->graph[k]) {
+        cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+      }
   LBM_CUDA(c, launch_init_eq(c->precision, c->p, c->flags, c->rho_m, c->ux_m, c->uy_m, c->f[0],
                              c->stream));
   LBM_CUDA(c, cudaMemsetAsync(c->f[1], 0, c->lattice_bytes, c->stream));
@@ -392,14 +395,16 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, cons
   if (c->status) return c->status;
   if (!rho) return LBM_EINVAL;
   const size_t N = (size_t)c->p.N;
-  if (c->rho_ref_auto) {  // smallest positive finite initial density
+  LBM_CUDA(c, cudaMemcpyAsync(c->rho_m, rho, N * 8, cudaMemcpyHostToDevice, c->stream));
+  if (c->rho_ref_auto) {  // smallest positive finite initial density, found on the device
+    // (mass_out is free scratch outside lbm_mass)
+    LBM_CUDA(c, launch_min_positive(c->rho_m, (long long)N, c->mass_out, c->stream));
     double m = 0.0;
-    for (size_t k = 0; k < N; ++k)
-      if (std::isfinite(rho[k]) && rho[k] > 0 && (m == 0.0 || rho[k] < m)) m = rho[k];
-    if (m > 0) c->p.rho_ref = m;
+    LBM_CUDA(c, cudaMemcpyAsync(&m, c->mass_out, 8, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (std::isfinite(m) && m > 0) c->p.rho_ref = m;
     finalize_consts(c->p);
   }
-  LBM_CUDA(c, cudaMemcpyAsync(c->rho_m, rho, N * 8, cudaMemcpyHostToDevice, c->stream));
   if (ux)
     LBM_CUDA(c, cudaMemcpyAsync(c->ux_m, ux, N * 8, cudaMemcpyHostToDevice, c->stream));
   else

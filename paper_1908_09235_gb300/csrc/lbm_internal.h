@@ -162,6 +162,8 @@ cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, cudaStream_t s);
 
 // ledger.cu
 int ledger_num_blocks(int N);
+// Smallest positive finite value of v[0..n) into *out (device), +inf if none.
+cudaError_t launch_min_positive(const double* v, long long n, double* out, cudaStream_t s);
 cudaError_t launch_mass(int precision, const DevParams& p, const void* f, const uint8_t* flags,
                         double* partials, int nblocks, double* result, int* err_flag,
                         cudaStream_t s);
@@ -227,6 +229,7 @@ struct lbm_ctx {
   bool initialized = false;
   int graph_steps = 32;  // time steps per captured graph
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  double graph_rho_ref = 0.0;  // rho_ref the captured graphs hold (kernel parameters by value)
   lbm_status status = LBM_OK;
   std::string msg;
   double T = 0.0;

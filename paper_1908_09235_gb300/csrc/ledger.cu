@@ -159,4 +159,39 @@ cudaError_t launch_droplet_rho(const DevParams& p, double cx, double cy, double 
   return cudaGetLastError();
 }
 
+// Smallest positive finite value of v[0..n): the automatic reference density of the deviation
+// formats.  Positive finite doubles order like their bit patterns as unsigned integers, so the
+// minimum is an exact atomicMin on the bits (order-independent, the same value as any serial
+// scan).  *out = +inf when there is no such value.
+__global__ void min_init_kernel(unsigned long long* out) { *out = 0x7ff0000000000000ULL; }
+
+__global__ void min_positive_kernel(const double* __restrict__ v, long long n,
+                                    unsigned long long* __restrict__ out) {
+  unsigned long long m = 0x7ff0000000000000ULL;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double x = v[k];
+    if (x > 0.0 && x < __longlong_as_double(0x7ff0000000000000LL)) {
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+      m = b < m ? b : m;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t < m ? t : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m != 0x7ff0000000000000ULL) atomicMin(out, m);
+}
+
+cudaError_t launch_min_positive(const double* v, long long n, double* out, cudaStream_t s) {
+  unsigned long long* o = reinterpret_cast<unsigned long long*>(out);
+  min_init_kernel<<<1, 1, 0, s>>>(o);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 1216) blocks = 1216;
+  if (blocks < 1) blocks = 1;
+  min_positive_kernel<<<(unsigned)blocks, 256, 0, s>>>(v, n, o);
+  return cudaGetLastError();
+}
+
 }  // namespace lbm
