@@ -16,7 +16,8 @@
  * builds the Carnahan-Starling constants and copies fields in and out.
  *
  * Conventions.  Node (i, j) sits at position (i, j) in lattice units, i in [0, nx), j in [0, ny);
- * its linear index is j*nx + i (row-major, y outer).  The outer box is periodic in x and y.
+ * its linear index is j*nx + i (row-major, y outer).  The outer box is periodic in x and y (x
+ * becomes a channel with a velocity inlet and an outlet after lbm_set_inflow, Sec. 5.1).
  * D2Q9 directions: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
  * All host arrays are caller-owned and are read or written only during the call.  Device state is
  * owned by the context and released by lbm_destroy.  Functions return an lbm_status; a non-zero
@@ -197,6 +198,10 @@ lbm_status lbm_flags(lbm_ctx* ctx, uint8_t* flags);
  * the capacity is too small (the count is still returned).  Blocks. */
 lbm_status lbm_links(lbm_ctx* ctx, int32_t* node, uint8_t* dir, double* q, int64_t* n_inout);
 
+/* Sizes and counters of the context (nodes, fluid nodes, boundary nodes, cut links, steps since
+ * the last initialisation, device bytes held, the absolute temperature of a Carnahan-Starling
+ * fluid, psi of the virtual wall density).  Host-only; never blocks and works on a context in
+ * error. */
 lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
 
 /* Channel flow past solid bodies (Sec. 5.1, steady flow past a circular cylinder): from the next
@@ -241,6 +246,9 @@ lbm_status lbm_mass_noalloc(const void* f, const uint8_t* flags, int32_t nx, int
                             int32_t* status_out, void* stream);
 
 /* ---- Batches: many lattices advanced together -------------------------------------------------
+ * (No counterpart in the paper, which advances one lattice at a time: batches serve many
+ * independent lattices of different sizes, step budgets and parameters at once, for throughput
+ * and for the serving loop of paper_1908_09235_gb300/serve.py.)
  * A batch holds up to max_domains lattices of one precision and one EOS kind.  One batch step is
  * three kernel launches for all of them (a persistent step kernel over a table of tiles, a
  * persistent boundary kernel over all boundary nodes, and a kernel that advances each lattice's

@@ -124,3 +124,18 @@ def test_batch_rejects_other_eos_and_full_batches(gpu_lib):
         b.add(_member(ws[1], lbm.MOD_B, lbm.FP32_DEV), 10)
     assert e.value.status == 2
     b.close()
+
+
+def test_full_batched_workload_sampled_members(gpu_lib):
+    # the 512-lattice workload of the benchmark, in its launch configuration (FP32 deviations,
+    # tuned tile height, graphs): sampled members give the same bits as the same lattice alone
+    # (diverging members included: their NaN pattern must match too)
+    ws = workloads.batched_domains()
+    b = lbm.Batch(lbm.FP32_DEV, lbm.EOS_CS, max_domains=len(ws))
+    slots = [b.add(_member(w, lbm.MOD_B, lbm.FP32_DEV), 10**9) for w in ws]
+    assert b.tune(3) in (8, 16, 32)
+    b.step(40)
+    for k in (0, 137, 311, 511):
+        fields, _ = _alone(ws[k], lbm.MOD_B, lbm.FP32_DEV, 40)
+        _same(b.fields(slots[k]), fields)
+    b.close()

@@ -353,3 +353,20 @@ def test_large_droplet_on_cylinder_full_size(gpu_lib, precision):
         tol = TOL32_NORM_100 if precision == lbm.FP32_DEV else TOL16_NORM_100
         assert rel <= tol, rel  # three steps
     lat.close()
+
+
+# ---- reduced precision at the largest configured size (8192^2): the mass ledger --------------
+@pytest.mark.parametrize("precision", [lbm.FP32_DEV, lbm.FP16_DEV])
+def test_reduced_precision_mass_at_8192(gpu_lib, precision):
+    L = 8192
+    w = workloads.droplet_on_cylinder(L, 600.0 / 4096 * L, 800.0 / 4096 * L)
+    eos = lbm.make_eos(lbm.EOS_CS, **w.eos)
+    rl, rv = lbm.lbm_coexistence(eos)
+    eos.rho_wall = rv
+    lat = lbm.Lattice(L, L, w.tau, lbm.MOD_B, circles=w.circles, eos=eos, precision=precision)
+    lat.init_droplet(*w.drop, rl, rv)
+    m0 = lat.mass()
+    lat.step(200)
+    # scheme B conserves mass; the FP64 wall-pass bookkeeping keeps the stored total to round-off
+    assert abs(lat.mass() / m0 - 1.0) < 1e-8
+    lat.close()
