@@ -257,7 +257,8 @@ TABLE1 = {20: {"scheme A": (1.90, 41.35, 2.130), "scheme B": (1.91, 41.56, 2.133
 def cylinder_wake(ux, uy, cx, cy, r, D):
     """Wake length 2L/D (L from the cylinder's rearmost point to where u_x on the centre line
     turns positive again) and separation angle (degrees from the rear stagnation point, where the
-    tangential velocity on a ring just outside the surface changes sign; mean of both halves)."""
+    tangential velocity changes sign on rings just outside the surface, mean of both halves,
+    extrapolated linearly from the rings to the surface)."""
     import numpy as np
     j = int(round(cy))
     row = ux[j]
@@ -274,21 +275,28 @@ def cylinder_wake(ux, uy, cx, cy, r, D):
         return ((1 - tx) * (1 - ty) * a[j0, i0] + tx * (1 - ty) * a[j0, i0 + 1] +
                 (1 - tx) * ty * a[j0 + 1, i0] + tx * ty * a[j0 + 1, i0 + 1])
 
-    rs = r + 1.5
-    angles = []
-    for side in (1.0, -1.0):
-        prev = None
-        for k in range(1, 1800):
-            th = np.radians(0.1 * k)
-            x, y = cx + rs * np.cos(th), cy + side * rs * np.sin(th)
-            # tangential velocity towards the front, mirrored onto the upper half (u_y is odd
-            # under the reflection y -> 2 cy - y, u_x even)
-            ut = -np.sin(th) * bilinear(ux, x, y) + side * np.cos(th) * bilinear(uy, x, y)
-            if prev is not None and prev > 0.0 >= ut:
-                angles.append(0.1 * (k - 1) + 0.1 * prev / (prev - ut))
-                break
-            prev = ut
-    theta = float(np.mean(angles)) if angles else float("nan")
+    def angle_at(rs):
+        angles = []
+        for side in (1.0, -1.0):
+            prev = None
+            for k in range(1, 1800):
+                th = np.radians(0.1 * k)
+                x, y = cx + rs * np.cos(th), cy + side * rs * np.sin(th)
+                # tangential velocity towards the front, mirrored onto the upper half (u_y is
+                # odd under the reflection y -> 2 cy - y, u_x even)
+                ut = -np.sin(th) * bilinear(ux, x, y) + side * np.cos(th) * bilinear(uy, x, y)
+                if prev is not None and prev > 0.0 >= ut:
+                    angles.append(0.1 * (k - 1) + 0.1 * prev / (prev - ut))
+                    break
+                prev = ut
+        return float(np.mean(angles)) if len(angles) == 2 else float("nan")
+
+    # rings from r + 1.5 (the nearest whose interpolation cells hold no solid node) outwards;
+    # the angle at the surface is their linear extrapolation to radius r
+    radii = np.array([1.5, 2.0, 2.5, 3.0]) + r
+    th = np.array([angle_at(v) for v in radii])
+    theta = float(np.polyval(np.polyfit(radii - r, th, 1), 0.0)) if np.all(np.isfinite(th)) \
+        else float("nan")
     return 2.0 * L / D, theta
 
 
@@ -598,7 +606,7 @@ def main():
     ap.add_argument("--cylinder-flow", action="store_true",
                     help="Sec. 5.1: flow past a cylinder at Re 20 and 40 against Table 1")
     ap.add_argument("--cyl-diameter", type=int, default=40)
-    ap.add_argument("--cyl-max-steps", type=int, default=200000)
+    ap.add_argument("--cyl-max-steps", type=int, default=400000)
     ap.add_argument("--precision-report", action="store_true",
                     help="FP32/FP16 deviation storage on long runs: mass drift and error vs FP64")
     ap.add_argument("--report-sides", default="2048,8192")
