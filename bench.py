@@ -434,6 +434,9 @@ def run_profile_case(args):
                       "fluid_nodes": info["n_fluid"]}), flush=True)
 
 
+SCHED_NAMES = ("strided", "claim", "claim_largest_first")
+
+
 def _batch_member(lbm, w):
     eos = lbm.make_eos(lbm.EOS_CS, **w["eos"])
     rl, rv = lbm.lbm_coexistence(eos)
@@ -444,7 +447,8 @@ def _batch_member(lbm, w):
 
 def run_batched(args):
     """512 uneven droplet-on-cylinder lattices (sides 64..512, seeded) in one batch: one set of
-    launches per time step under a CUDA graph, tile height chosen by the batch's tuner.
+    launches per time step under a CUDA graph, tile height and tile-queue schedule chosen by the
+    batch's tuner.
     Compared with the plain loop that advances one FP64 lattice at a time."""
     import torch
 
@@ -455,6 +459,7 @@ def run_batched(args):
     b = lbm.Batch(prec, lbm.EOS_CS, max_domains=len(ws))
     slots = [b.add(_batch_member(lbm, w), 10**9) for w in ws]
     rows = b.tune(3)
+    trials = b.tune_trials()
     info = b.info()
     b.step(args.warmup)
     torch.cuda.synchronize()
@@ -497,7 +502,10 @@ def run_batched(args):
             "config": {"workload": "batched_droplets_%d" % len(ws), "storage": args.precision,
                        "scheme": "mod_b", "lattices": info["active"], "nodes": info["nodes"],
                        "fluid_nodes": info["fluid_nodes"], "tiles": info["tiles"],
-                       "tile": [info["tile_cols"], info["tile_rows"]], "graph": True},
+                       "tile": [info["tile_cols"], info["tile_rows"]],
+                       "schedule": SCHED_NAMES[info["schedule"]], "graph": True},
+            "tuner_ms_per_launch": {"%dx%d/%s" % (info["tile_cols"], r, SCHED_NAMES[sc]):
+                                    round(ms, 4) for r, sc, ms in trials},
             "split_ms_per_step": {"step_kernel": round(split[1] / 5, 4),
                                   "boundary_and_advance": round(split[2] / 5, 4)},
             "unstable_lattices": unstable,

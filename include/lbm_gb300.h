@@ -250,7 +250,7 @@ lbm_status lbm_mass_noalloc(const void* f, const uint8_t* flags, int32_t nx, int
  * independent lattices of different sizes, step budgets and parameters at once, for throughput
  * and for the serving loop of paper_1908_09235_gb300/serve.py.)
  * A batch holds up to max_domains lattices of one precision and one EOS kind.  One batch step is
- * three kernel launches for all of them (a persistent step kernel over a table of tiles, a
+ * three kernel launches for all of them (a persistent step kernel over a queue of tiles, a
  * persistent boundary kernel over all boundary nodes, and a kernel that advances each lattice's
  * state), replayed from a CUDA graph; lattices join and leave between steps and each stops at its
  * own step budget.  A lattice gives the same bits alone (lbm_step) and inside any batch. */
@@ -265,16 +265,38 @@ typedef struct {
   double cx, cy, R, W, rho_in, rho_out;
 } lbm_domain;
 
+/* How the CTAs of a batch's persistent step kernel work through its queue of tiles.  The
+ * tiles of one lattice stand together, row by row; results are the same bits under every
+ * schedule and tile height (only the order of independent tiles changes). */
+typedef enum {
+  LBM_SCHED_STRIDED = 0,              /* CTA k takes tiles k, k + G, k + 2G, ... (G CTAs);
+                                         lattices in slot order                            */
+  LBM_SCHED_CLAIM = 1,                /* CTAs claim the next tile from a device counter;
+                                         lattices in slot order                            */
+  LBM_SCHED_CLAIM_LARGEST_FIRST = 2   /* CTAs claim tiles; lattices by tile count, largest
+                                         first (ties in slot order)                        */
+} lbm_schedule;
+
 typedef struct {
   int32_t active;          /* lattices in the batch                                         */
   int32_t tiles;           /* tiles in the current table (-1 before the first step)         */
   int32_t tile_rows, tile_cols;
   int64_t nodes, fluid_nodes, boundary_links;
   int64_t device_bytes;    /* device memory of the batch and its lattices                   */
+  int32_t schedule;        /* lbm_schedule of the tile queue                                */
+  int32_t pad;
 } lbm_batch_info_t;
 
+/* One candidate timed by lbm_batch_tune: tile height, schedule, mean step-kernel time. */
+typedef struct {
+  int32_t tile_rows;
+  int32_t schedule;
+  double ms;
+} lbm_tune_trial;
+
 /* opt: stream and allocation hook for the batch and every lattice in it (precision is taken
- * from the argument).  LBM_EINVAL for bad arguments. */
+ * from the argument).  Starts with 16-row tiles and LBM_SCHED_CLAIM (lbm_batch_tune,
+ * lbm_batch_set_schedule change them).  LBM_EINVAL for bad arguments. */
 lbm_status lbm_batch_create(int32_t precision, int32_t eos_kind, int32_t max_domains,
                             const lbm_options* opt, lbm_batch** out);
 /* Create, initialise and add a lattice with a budget of `steps` time steps; *slot receives its
@@ -297,9 +319,18 @@ lbm_status lbm_batch_poll(lbm_batch* b, int32_t n, int64_t* steps_left);
 /* The lattice's context, current as of this call, for lbm_mass, lbm_fields, lbm_info (blocks).
  * It stays owned by the batch; do not step or destroy it directly. */
 lbm_status lbm_batch_domain(lbm_batch* b, int32_t slot, lbm_ctx** ctx);
-/* Time the step kernel for each tile height (8, 16, 32 rows; FP64: 8, 16) on the current batch
- * without changing any state, keep the fastest; *tile_rows receives it. */
+/* Time the step kernel (mean of trial_steps launches after two warm-up launches) for each tile
+ * height (8, 16, 32 rows; FP64: 8, 16) under each lbm_schedule on the current batch, without
+ * changing any lattice's state, and keep the fastest pair; *tile_rows receives its height and
+ * lbm_batch_info its schedule.  LBM_EINVAL for trial_steps < 1. */
 lbm_status lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* tile_rows);
+/* The candidates of the last lbm_batch_tune in the order timed: up to max into out, their
+ * number into *n (0 before any tuning). */
+lbm_status lbm_batch_tune_trials(const lbm_batch* b, int32_t max, lbm_tune_trial* out,
+                                 int32_t* n);
+/* Set the tile height (8, 16, 32; FP64: 8, 16) and schedule by hand (takes effect at the next
+ * step; a captured graph is dropped).  LBM_EINVAL for other values. */
+lbm_status lbm_batch_set_schedule(lbm_batch* b, int32_t tile_rows, int32_t schedule);
 lbm_status lbm_batch_info(lbm_batch* b, lbm_batch_info_t* out);
 /* Device bytes a lattice would need in a batch of the given precision (upper estimate). */
 lbm_status lbm_domain_bytes(const lbm_domain* d, int32_t precision, int64_t* bytes);

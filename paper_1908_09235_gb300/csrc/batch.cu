@@ -3,13 +3,15 @@
 // Every lattice of a batch is an ordinary context (its own geometry, link list, two lattices),
 // created by lbm_create with the batch's precision, stream and allocation hook.  One time step of
 // the batch is three launches whatever the number of lattices:
-//   batch_step_kernel      persistent grid over a table of tiles (lattice, x0, y0)
+//   batch_step_kernel      persistent grid over a queue of tiles (lattice, x0, y0)
 //   batch_boundary_kernel  persistent grid of 8-lane groups over (lattice, boundary node) items
 //   batch_advance_kernel   flips each lattice's current buffer and counts down its step budget
 // The tables live at fixed device addresses and the number of tiles and items is read on the
 // device, so a captured CUDA graph stays valid while lattices join and leave; lattices whose
-// budget is spent are skipped.  The per-node arithmetic is the single-lattice arithmetic, so a
+// budget is spent are skipped.  The tuner picks the tile height and the queue's schedule (how
+// CTAs take tiles, in which order the lattices' tiles stand).  The per-node arithmetic is the single-lattice arithmetic, so a
 // lattice gives the same bits alone and inside any batch, with any tile shape.
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -30,13 +32,15 @@ struct lbm_batch {
   std::vector<char> uploaded;  // slot's entry in the device table is current
   // device tables
   BatchDomain* d_doms = nullptr;
-  int* d_counts = nullptr;  // [0] tiles, [1] boundary items
+  int* d_counts = nullptr;  // [0] tiles, [1] boundary items, [2] tile claim counter
   int4* d_tiles = nullptr;
   int2* d_items = nullptr;
   int cap_tiles = 0, cap_items = 0;
   std::vector<std::pair<void*, size_t>> blocks;
   int n_tiles = 0, n_items = 0;
   int ry = 0;  // tile rows per thread (tile height 8 ry)
+  int sched = LBM_SCHED_STRIDED;  // lbm_schedule of the tile queue
+  std::vector<lbm_tune_trial> trials;  // of the last lbm_batch_tune
   int step_grid = 0, bnd_grid = 0;
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;
@@ -134,14 +138,29 @@ BatchDomain describe(lbm_ctx* c, long long steps) {
   return d;
 }
 
-// Rebuild the tile and item tables from the active lattices and upload everything.
+int* claim_counter(lbm_batch* b) {
+  return b->sched == LBM_SCHED_STRIDED ? nullptr : b->d_counts + 2;
+}
+
+// Rebuild the tile and item tables from the active lattices and upload everything.  The tiles
+// of a lattice stand together in row-major order; the lattices follow in slot order, or by tile
+// count, largest first, for LBM_SCHED_CLAIM_LARGEST_FIRST (ties in slot order).
 lbm_status upload_tables(lbm_batch* b) {
   const int TH = batch_tile_rows(b->ry), TW = batch_tile_cols();
+  std::vector<int> order;
+  for (int d = 0; d < b->max_domains; ++d)
+    if (b->slots[d]) order.push_back(d);
+  auto n_tiles_of = [&](int d) {
+    const lbm_ctx* c = b->slots[d];
+    return (long long)((c->p.nx + TW - 1) / TW) * ((c->p.ny + TH - 1) / TH);
+  };
+  if (b->sched == LBM_SCHED_CLAIM_LARGEST_FIRST)
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int u, int v) { return n_tiles_of(u) > n_tiles_of(v); });
   std::vector<int4> tiles;
   std::vector<int2> items;
-  for (int d = 0; d < b->max_domains; ++d) {
+  for (int d : order) {
     lbm_ctx* c = b->slots[d];
-    if (!c) continue;
     for (int y0 = 0; y0 < c->p.ny; y0 += TH)
       for (int x0 = 0; x0 < c->p.nx; x0 += TW) tiles.push_back(make_int4(d, x0, y0, 0));
     for (int k = 0; k < (int)c->nb; ++k) items.push_back(make_int2(d, k));
@@ -162,7 +181,7 @@ lbm_status upload_tables(lbm_batch* b) {
   }
   b->n_tiles = (int)tiles.size();
   b->n_items = (int)items.size();
-  int counts[2] = {b->n_tiles, b->n_items};
+  int counts[3] = {b->n_tiles, b->n_items, 0};
   if (!tiles.empty())
     BCUDA(b, cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(),
                              cudaMemcpyHostToDevice, b->stream));
@@ -181,11 +200,11 @@ lbm_status upload_tables(lbm_batch* b) {
 lbm_status one_step(lbm_batch* b, cudaStream_t s, cudaEvent_t e_mid = nullptr,
                     cudaEvent_t e_end = nullptr) {
   BCUDA(b, launch_batch_step(b->precision, b->eos, b->ry, b->d_doms, b->d_tiles, b->d_counts,
-                             b->step_grid, s));
+                             claim_counter(b), b->step_grid, s));
   if (e_mid) BCUDA(b, cudaEventRecord(e_mid, s));
   BCUDA(b, launch_batch_boundary(b->precision, b->d_doms, b->d_items, b->d_counts + 1,
                                  b->bnd_grid, s));
-  BCUDA(b, launch_batch_advance(b->d_doms, b->max_domains, s));
+  BCUDA(b, launch_batch_advance(b->d_doms, b->max_domains, b->d_counts + 2, s));
   if (e_end) BCUDA(b, cudaEventRecord(e_end, s));
   return LBM_OK;
 }
@@ -223,7 +242,8 @@ lbm_status lbm_batch_create(int32_t precision, int32_t eos_kind, int32_t max_dom
   b->slots.assign(max_domains, nullptr);
   b->h_doms.assign(max_domains, BatchDomain{});
   b->uploaded.assign(max_domains, 0);
-  b->ry = precision == LBM_FP64 ? 2 : 4;
+  b->ry = 2;  // 16-row tiles, claimed: the fastest pair on the 512-lattice workload
+  b->sched = LBM_SCHED_CLAIM;
   b->step_grid = batch_step_grid(precision, eos_kind, b->ry);
   b->bnd_grid = 152 * 8;
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -411,46 +431,84 @@ lbm_status lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* tile_rows)
   lbm_status st = ready(b);
   if (st != LBM_OK) return st;
   const int cands[3] = {1, 2, 4};
-  int best = b->ry;
+  const int scheds[3] = {LBM_SCHED_STRIDED, LBM_SCHED_CLAIM, LBM_SCHED_CLAIM_LARGEST_FIRST};
+  int best = b->ry, best_sched = b->sched;
   float best_ms = 1e30f;
+  b->trials.clear();
   cudaEvent_t e0, e1;
   BCUDA(b, cudaEventCreate(&e0));
   BCUDA(b, cudaEventCreate(&e1));
+  // Only the step kernel runs: it writes the not-yet-current buffer of every lattice, which
+  // the next real step overwrites, so the state does not change.  The claim counter is zeroed
+  // before every launch (the advance kernel does it in a real step), for every schedule alike.
+  auto launch = [&](int ry) {
+    if (cudaMemsetAsync(b->d_counts + 2, 0, sizeof(int), b->stream) != cudaSuccess ||
+        launch_batch_step(b->precision, b->eos, ry, b->d_doms, b->d_tiles, b->d_counts,
+                          claim_counter(b), b->step_grid, b->stream) != cudaSuccess)
+      st = bfail(b, LBM_ECUDA, "tuning launch");
+  };
   for (int ry : cands) {
     if (b->precision == LBM_FP64 && ry == 4) continue;  // register budget of FP64
-    b->ry = ry;
-    b->step_grid = batch_step_grid(b->precision, b->eos, ry);
-    st = upload_tables(b);
-    if (st != LBM_OK) break;
-    // Only the step kernel runs: it writes the not-yet-current buffer of every lattice, which
-    // the next real step overwrites, so the state does not change.
-    for (int k = 0; k < 2 && st == LBM_OK; ++k)  // warm-up
-      if (launch_batch_step(b->precision, b->eos, ry, b->d_doms, b->d_tiles, b->d_counts,
-                            b->step_grid, b->stream) != cudaSuccess)
-        st = bfail(b, LBM_ECUDA, "tuning launch");
-    cudaEventRecord(e0, b->stream);
-    for (int k = 0; k < trial_steps && st == LBM_OK; ++k)
-      if (launch_batch_step(b->precision, b->eos, ry, b->d_doms, b->d_tiles, b->d_counts,
-                            b->step_grid, b->stream) != cudaSuccess)
-        st = bfail(b, LBM_ECUDA, "tuning launch");
-    cudaEventRecord(e1, b->stream);
-    cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (st == LBM_OK && ms < best_ms) {
-      best_ms = ms;
-      best = ry;
+    for (int sc : scheds) {
+      b->ry = ry;
+      b->sched = sc;
+      b->step_grid = batch_step_grid(b->precision, b->eos, ry);
+      st = upload_tables(b);
+      if (st != LBM_OK) break;
+      for (int k = 0; k < 2 && st == LBM_OK; ++k) launch(ry);  // warm-up
+      cudaEventRecord(e0, b->stream);
+      for (int k = 0; k < trial_steps && st == LBM_OK; ++k) launch(ry);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (st != LBM_OK) break;
+      b->trials.push_back(lbm_tune_trial{batch_tile_rows(ry), sc, (double)ms / trial_steps});
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = ry;
+        best_sched = sc;
+      }
     }
+    if (st != LBM_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  // leave the counter at 0 for the next real step
+  if (cudaMemsetAsync(b->d_counts + 2, 0, sizeof(int), b->stream) != cudaSuccess && st == LBM_OK)
+    st = bfail(b, LBM_ECUDA, "cudaMemsetAsync");
   if (st != LBM_OK) return st;
   drop_graph(b);
   b->ry = best;
+  b->sched = best_sched;
   b->step_grid = batch_step_grid(b->precision, b->eos, best);
   st = upload_tables(b);
   if (tile_rows) *tile_rows = batch_tile_rows(best);
   return st;
+}
+
+lbm_status lbm_batch_tune_trials(const lbm_batch* b, int32_t max, lbm_tune_trial* out,
+                                 int32_t* n) {
+  if (!b || !n || max < 0 || (max > 0 && !out)) return LBM_EINVAL;
+  *n = (int32_t)b->trials.size();
+  for (int32_t k = 0; k < max && k < *n; ++k) out[k] = b->trials[k];
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_schedule(lbm_batch* b, int32_t tile_rows, int32_t schedule) {
+  if (!b) return LBM_EINVAL;
+  if (schedule < LBM_SCHED_STRIDED || schedule > LBM_SCHED_CLAIM_LARGEST_FIRST) return LBM_EINVAL;
+  int ry = 0;
+  for (int r : {1, 2, 4})
+    if (batch_tile_rows(r) == tile_rows) ry = r;
+  if (ry == 0 || (b->precision == LBM_FP64 && ry == 4)) return LBM_EINVAL;
+  if (b->status) return b->status;
+  drop_graph(b);
+  b->ry = ry;
+  b->sched = schedule;
+  b->step_grid = batch_step_grid(b->precision, b->eos, ry);
+  b->dirty = true;
+  return LBM_OK;
 }
 
 lbm_status lbm_batch_info(lbm_batch* b, lbm_batch_info_t* o) {
@@ -468,6 +526,7 @@ lbm_status lbm_batch_info(lbm_batch* b, lbm_batch_info_t* o) {
   o->tiles = b->dirty ? -1 : b->n_tiles;
   o->tile_rows = batch_tile_rows(b->ry);
   o->tile_cols = batch_tile_cols();
+  o->schedule = b->sched;
   return LBM_OK;
 }
 

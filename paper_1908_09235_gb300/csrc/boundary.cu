@@ -385,8 +385,9 @@ __global__ void __launch_bounds__(128) batch_boundary_kernel(const BatchDomain* 
   }
 }
 
-__global__ void batch_advance_kernel(BatchDomain* __restrict__ doms, int n) {
+__global__ void batch_advance_kernel(BatchDomain* __restrict__ doms, int n, int* claim) {
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d == 0) *claim = 0;  // the step kernel of the next step claims tiles from 0
   if (d < n && doms[d].steps_left > 0) {
     doms[d].cur ^= 1;
     --doms[d].steps_left;
@@ -458,9 +459,9 @@ cudaError_t launch_batch_boundary(int precision, const BatchDomain* doms, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, cudaStream_t s) {
+cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, int* claim, cudaStream_t s) {
   if (n_doms <= 0) return cudaSuccess;
-  batch_advance_kernel<<<(n_doms + 127) / 128, 128, 0, s>>>(doms, n_doms);
+  batch_advance_kernel<<<(n_doms + 127) / 128, 128, 0, s>>>(doms, n_doms, claim);
   return cudaGetLastError();
 }
 

@@ -154,11 +154,14 @@ cudaError_t launch_open_x(int precision, const DevParams& p, void* fb, const uin
 int batch_tile_rows(int ry);
 int batch_tile_cols();
 int batch_step_grid(int precision, int eos, int ry);
+// claim: the tile counter of the claiming work queue, or nullptr for the strided one
 cudaError_t launch_batch_step(int precision, int eos, int ry, const BatchDomain* doms,
-                              const int4* tiles, const int* n_tiles, int grid, cudaStream_t s);
+                              const int4* tiles, const int* n_tiles, int* claim, int grid,
+                              cudaStream_t s);
 cudaError_t launch_batch_boundary(int precision, const BatchDomain* doms, const int2* items,
                                   const int* n_items, int grid, cudaStream_t s);
-cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, cudaStream_t s);
+// also resets the tile counter *claim for the next step
+cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, int* claim, cudaStream_t s);
 
 // ledger.cu
 int ledger_num_blocks(int N);

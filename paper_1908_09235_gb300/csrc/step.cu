@@ -31,24 +31,38 @@ __global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 :
                                 blockIdx.y * TYT * RY, psi_s);
 }
 
-// Many lattices in one launch: a persistent grid walks a table of tiles (domain, x0, y0).  Tiles
-// of domains whose step budget is spent are skipped.  RY (rows per thread, so the tile height
-// 8 RY) is the tile shape chosen by the batch's tuner.
+// Many lattices in one launch: a persistent grid works through a queue of tiles (domain, x0,
+// y0).  With claim == nullptr each CTA takes every gridDim.x-th tile; otherwise CTAs claim the
+// next tile from the device counter *claim (reset to 0 by the advance kernel after every step),
+// one atomic per tile, taken while the previous tile is still being worked on.  Tiles of domains
+// whose step budget is spent are skipped.  RY (rows per thread, so the tile height 8 RY) and the
+// queue are chosen by the batch's tuner.
 template <typename S, int EOS, int RY>
 __global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 : 2)
     batch_step_kernel(const BatchDomain* __restrict__ doms, const int4* __restrict__ tiles,
-                      const int* __restrict__ n_tiles) {
+                      const int* __restrict__ n_tiles, int* __restrict__ claim) {
   using C = typename StoreTraits<S>::C;
   __shared__ C psi_s[TYT * RY + 2][TX + 2];
+  __shared__ int next_s[2];  // claimed tiles, double-buffered across the end-of-tile barrier
+  const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
   const int nt = *n_tiles;
-  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+  int t = blockIdx.x;
+  if (claim) {
+    if (lead) next_s[0] = atomicAdd(claim, 1);
+    __syncthreads();
+    t = next_s[0];
+  }
+  for (int k = 1; t < nt; ++k) {
+    if (claim && lead) next_s[k & 1] = atomicAdd(claim, 1);
     const int4 tile = tiles[t];  // (domain, x0, y0, -)
     const BatchDomain& D = doms[tile.x];
-    if (D.steps_left <= 0) continue;
-    const int cur = D.cur;
-    step_tile<S, EOS, false, RY>(D.p, D.f[cur], D.f[cur ^ 1], D.flags, D.rho_m, D.ux_m, D.uy_m,
-                                 tile.y, tile.z, psi_s);
-    __syncthreads();  // psi_s is reused by the next tile
+    if (D.steps_left > 0) {
+      const int cur = D.cur;
+      step_tile<S, EOS, false, RY>(D.p, D.f[cur], D.f[cur ^ 1], D.flags, D.rho_m, D.ux_m,
+                                   D.uy_m, tile.y, tile.z, psi_s);
+    }
+    __syncthreads();  // psi_s is reused by the next tile; next_s[k & 1] is visible
+    t = claim ? next_s[k & 1] : t + gridDim.x;
   }
 }
 
@@ -82,29 +96,30 @@ cudaError_t launch_s(const DevParams& p, const void* fa, void* fb, const uint8_t
 }
 
 template <typename S, int EOS, int RY>
-cudaError_t launch_batch_t(const BatchDomain* doms, const int4* tiles, const int* n_tiles, int grid,
-                           cudaStream_t s) {
-  batch_step_kernel<S, EOS, RY><<<grid, dim3(TX, TYT), 0, s>>>(doms, tiles, n_tiles);
+cudaError_t launch_batch_t(const BatchDomain* doms, const int4* tiles, const int* n_tiles,
+                           int* claim, int grid, cudaStream_t s) {
+  batch_step_kernel<S, EOS, RY><<<grid, dim3(TX, TYT), 0, s>>>(doms, tiles, n_tiles, claim);
   return cudaGetLastError();
 }
 
 template <typename S, int RY>
 cudaError_t launch_batch_e(int eos, const BatchDomain* doms, const int4* tiles, const int* n_tiles,
-                           int grid, cudaStream_t s) {
+                           int* claim, int grid, cudaStream_t s) {
   switch (eos) {
-    case LBM_EOS_EXP: return launch_batch_t<S, LBM_EOS_EXP, RY>(doms, tiles, n_tiles, grid, s);
-    case LBM_EOS_CS: return launch_batch_t<S, LBM_EOS_CS, RY>(doms, tiles, n_tiles, grid, s);
-    default: return launch_batch_t<S, LBM_EOS_NONE, RY>(doms, tiles, n_tiles, grid, s);
+    case LBM_EOS_EXP:
+      return launch_batch_t<S, LBM_EOS_EXP, RY>(doms, tiles, n_tiles, claim, grid, s);
+    case LBM_EOS_CS: return launch_batch_t<S, LBM_EOS_CS, RY>(doms, tiles, n_tiles, claim, grid, s);
+    default: return launch_batch_t<S, LBM_EOS_NONE, RY>(doms, tiles, n_tiles, claim, grid, s);
   }
 }
 
 template <typename S>
 cudaError_t launch_batch_s(int eos, int ry, const BatchDomain* doms, const int4* tiles,
-                           const int* n_tiles, int grid, cudaStream_t s) {
-  if (ry == 1) return launch_batch_e<S, 1>(eos, doms, tiles, n_tiles, grid, s);
-  if (ry == 2) return launch_batch_e<S, 2>(eos, doms, tiles, n_tiles, grid, s);
+                           const int* n_tiles, int* claim, int grid, cudaStream_t s) {
+  if (ry == 1) return launch_batch_e<S, 1>(eos, doms, tiles, n_tiles, claim, grid, s);
+  if (ry == 2) return launch_batch_e<S, 2>(eos, doms, tiles, n_tiles, claim, grid, s);
   if constexpr (sizeof(typename Pop<S>::C) == 4) {
-    if (ry == 4) return launch_batch_e<S, 4>(eos, doms, tiles, n_tiles, grid, s);
+    if (ry == 4) return launch_batch_e<S, 4>(eos, doms, tiles, n_tiles, claim, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -139,10 +154,13 @@ int batch_step_grid(int precision, int eos, int ry) {
 }
 
 cudaError_t launch_batch_step(int precision, int eos, int ry, const BatchDomain* doms,
-                              const int4* tiles, const int* n_tiles, int grid, cudaStream_t s) {
-  if (precision == LBM_FP32_DEV) return launch_batch_s<float>(eos, ry, doms, tiles, n_tiles, grid, s);
-  if (precision == LBM_FP16_DEV) return launch_batch_s<__half>(eos, ry, doms, tiles, n_tiles, grid, s);
-  return launch_batch_s<double>(eos, ry, doms, tiles, n_tiles, grid, s);
+                              const int4* tiles, const int* n_tiles, int* claim, int grid,
+                              cudaStream_t s) {
+  if (precision == LBM_FP32_DEV)
+    return launch_batch_s<float>(eos, ry, doms, tiles, n_tiles, claim, grid, s);
+  if (precision == LBM_FP16_DEV)
+    return launch_batch_s<__half>(eos, ry, doms, tiles, n_tiles, claim, grid, s);
+  return launch_batch_s<double>(eos, ry, doms, tiles, n_tiles, claim, grid, s);
 }
 
 cudaError_t launch_step(int precision, const DevParams& p, const void* fa, void* fb,

@@ -33,7 +33,10 @@ EXPORTS = ("lbm_create", "lbm_coexistence", "lbm_init_fields", "lbm_init_droplet
            "lbm_batch_set_steps", "lbm_batch_step", "lbm_batch_step_timed", "lbm_batch_progress",
            "lbm_batch_domain", "lbm_batch_tune", "lbm_batch_info", "lbm_domain_bytes",
            "lbm_batch_last_error", "lbm_batch_destroy", "lbm_batch_poll", "lbm_set_inflow",
-           "lbm_force")
+           "lbm_force", "lbm_batch_tune_trials", "lbm_batch_set_schedule")
+
+# lbm_schedule: how the CTAs of a batch's step kernel take tiles from its queue
+SCHED_STRIDED, SCHED_CLAIM, SCHED_CLAIM_LARGEST_FIRST = 0, 1, 2
 
 
 class LBMError(RuntimeError):
@@ -87,7 +90,12 @@ class Domain(C.Structure):
 class BatchInfo(C.Structure):
     _fields_ = [("active", C.c_int32), ("tiles", C.c_int32), ("tile_rows", C.c_int32),
                 ("tile_cols", C.c_int32), ("nodes", C.c_int64), ("fluid_nodes", C.c_int64),
-                ("boundary_links", C.c_int64), ("device_bytes", C.c_int64)]
+                ("boundary_links", C.c_int64), ("device_bytes", C.c_int64),
+                ("schedule", C.c_int32), ("pad", C.c_int32)]
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("tile_rows", C.c_int32), ("schedule", C.c_int32), ("ms", C.c_double)]
 
 
 _lib = None
@@ -146,6 +154,9 @@ def load_library(build_if_missing=True):
             "lbm_batch_poll": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int64)]),
             "lbm_set_inflow": (C.c_int, [P, C.c_double]),
             "lbm_force": (C.c_int, [P, D, D]),
+            "lbm_batch_tune_trials": (C.c_int, [P, C.c_int32, C.POINTER(TuneTrial),
+                                                C.POINTER(C.c_int32)]),
+            "lbm_batch_set_schedule": (C.c_int, [P, C.c_int32, C.c_int32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -499,9 +510,21 @@ class Batch:
         return lbm_fields(self.ctx(slot), nx, ny)
 
     def tune(self, trial_steps=5):
+        """time every tile height and schedule, keep the fastest; returns the tile height"""
         rows = C.c_int32()
         self._chk(load_library().lbm_batch_tune(self.b, int(trial_steps), C.byref(rows)))
         return rows.value
+
+    def tune_trials(self):
+        """[(tile_rows, schedule, ms per step-kernel launch)] of the last tune, in timed order"""
+        n = C.c_int32()
+        self._chk(load_library().lbm_batch_tune_trials(self.b, 0, None, C.byref(n)))
+        arr = (TuneTrial * max(1, n.value))()
+        self._chk(load_library().lbm_batch_tune_trials(self.b, n.value, arr, C.byref(n)))
+        return [(t.tile_rows, t.schedule, t.ms) for t in arr[:n.value]]
+
+    def set_schedule(self, tile_rows, schedule):
+        self._chk(load_library().lbm_batch_set_schedule(self.b, int(tile_rows), int(schedule)))
 
     def info(self):
         i = BatchInfo()

@@ -71,20 +71,65 @@ def test_batch_members_match_standalone_runs(gpu_lib, precision):
     b.close()
 
 
-def test_tile_shape_does_not_change_results(gpu_lib):
-    ws = _stable_members(4, workloads.SEED + 1)
-    results = []
-    for rows in (None, "tuned"):
-        b = lbm.Batch(lbm.FP32_DEV, lbm.EOS_CS, max_domains=4)
-        slots = [b.add(_member(w, lbm.MOD_B, lbm.FP32_DEV), 40) for w in ws]
-        if rows == "tuned":
-            chosen = b.tune(3)
-            assert chosen in (8, 16, 32)
-        b.step(40)
-        results.append([b.fields(s) for s in slots])
-        b.close()
-    for a, c in zip(*results):
+def _run_with(ws, precision, rows_sched, steps=40):
+    b = lbm.Batch(precision, lbm.EOS_CS, max_domains=len(ws))
+    slots = [b.add(_member(w, lbm.MOD_B, precision), steps) for w in ws]
+    if rows_sched == "tuned":
+        assert b.tune(3) in (8, 16, 32)
+    elif rows_sched is not None:
+        b.set_schedule(*rows_sched)
+    b.step(steps)
+    info = b.info()
+    out = [b.fields(s) for s in slots]
+    b.close()
+    return out, info
+
+
+SCHEDS = (lbm.SCHED_STRIDED, lbm.SCHED_CLAIM, lbm.SCHED_CLAIM_LARGEST_FIRST)
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_DEV])
+def test_tile_shape_and_schedule_do_not_change_results(gpu_lib, precision):
+    # uneven sides, so the largest-first order differs from the slot order
+    ws = _stable_members(5, workloads.SEED + 1)
+    ref, _ = _run_with(ws, precision, None)
+    rows = (8, 16) if precision == lbm.FP64 else (8, 16, 32)
+    for r in rows:
+        for sc in SCHEDS:
+            out, info = _run_with(ws, precision, (r, sc))
+            assert (info["tile_rows"], info["schedule"]) == (r, sc)
+            for a, c in zip(ref, out):
+                _same(a, c)
+    out, info = _run_with(ws, precision, "tuned")
+    assert info["schedule"] in SCHEDS
+    for a, c in zip(ref, out):
         _same(a, c)
+
+
+def test_tuner_times_every_tile_height_and_schedule(gpu_lib):
+    ws = _stable_members(4, workloads.SEED + 2)
+    b = lbm.Batch(lbm.FP32_DEV, lbm.EOS_CS, max_domains=4)
+    for w in ws:
+        b.add(_member(w, lbm.MOD_B, lbm.FP32_DEV), 100)
+    assert b.tune_trials() == []
+    rows = b.tune(2)
+    trials = b.tune_trials()
+    assert [(r, s) for r, s, _ in trials] == [(r, s) for r in (8, 16, 32) for s in SCHEDS]
+    best = min(trials, key=lambda t: t[2])
+    info = b.info()
+    assert (rows, info["schedule"]) == best[:2] == (info["tile_rows"], info["schedule"])
+    assert all(t[2] > 0 for t in trials)
+    # tuning changed no state: every lattice still has its full budget
+    assert all(b.progress(s) == (0, 100) for s in range(4))
+    with pytest.raises(lbm.LBMError):
+        b.set_schedule(12, lbm.SCHED_CLAIM)
+    with pytest.raises(lbm.LBMError):
+        b.set_schedule(16, 7)
+    b.close()
+    b = lbm.Batch(lbm.FP64, lbm.EOS_CS, max_domains=2)
+    with pytest.raises(lbm.LBMError):
+        b.set_schedule(32, lbm.SCHED_STRIDED)  # FP64 register budget: 8 or 16 rows
+    b.close()
 
 
 def test_batched_lattice_matches_oracle(gpu_lib):
