@@ -12,5 +12,5 @@ from .binding import (  # noqa: F401
     HBB, FH, MLS, BOUZIDI_L, BOUZIDI_Q, ZHAO_YONG, MOD_A, MOD_B, BAO, BOUZIDI_L_A,
     EOS_NONE, EOS_EXP, EOS_CS, SCHEME_NAMES,
     OracleSim, feq, guo, collide_node, psi, cs_pressure, force_from_psi, cs_critical,
-    cs_coexistence, build_oracle, library_path,
+    cs_coexistence, build_oracle, library_path, num_threads,
 )

@@ -24,23 +24,24 @@ SCHEME_NAMES = {
 EOS_NONE, EOS_EXP, EOS_CS = 0, 1, 2
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}  # openmp flag -> loaded library
 
 
 def library_path(openmp=False):
     return os.path.join(BUILD_DIR, "liblbm_oracle_omp.so" if openmp else "liblbm_oracle.so")
 
 
-def build_oracle(force=False):
-    """Compile the oracle with gcc.  Returns the path of the shared library."""
+def build_oracle(force=False, openmp=False):
+    """Compile the oracle with gcc (openmp: the same source with -fopenmp, its node loops on all
+    host cores).  Returns the path of the shared library."""
     os.makedirs(BUILD_DIR, exist_ok=True)
-    out = library_path()
+    out = library_path(openmp)
     newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
     if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
         tmp = out + ".%d.tmp" % os.getpid()
         subprocess.check_call(
             ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared",
-             SRC, "-o", tmp, "-lm"])
+             *(["-fopenmp"] if openmp else []), SRC, "-o", tmp, "-lm"])
         os.replace(tmp, out)
     return out
 
@@ -66,12 +67,11 @@ _D = C.POINTER(C.c_double)
 _P = C.c_void_p
 
 
-def _load():
-    global _lib
+def _load(openmp=False):
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = C.CDLL(build_oracle())
+        if openmp in _libs:
+            return _libs[openmp]
+        lib = C.CDLL(build_oracle(openmp=openmp))
         sig = {
             "or_feq": (None, [C.c_double, C.c_double, C.c_double, _D]),
             "or_guo": (None, [C.c_double] * 5 + [_D]),
@@ -99,13 +99,19 @@ def _load():
             "or_fallbacks": (C.c_long, [_P]),
             "or_set_inflow": (None, [_P, C.c_double]),
             "or_force": (None, [_P, _D, _D]),
+            "or_num_threads": (C.c_int, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = lib
+        _libs[openmp] = lib
         return lib
+
+
+def num_threads(openmp=False):
+    """Threads the oracle's per-node loops use in the serial (1) or the -fopenmp build."""
+    return _load(openmp).or_num_threads()
 
 
 def _dptr(a):
@@ -183,10 +189,11 @@ def cs_coexistence(a, b, R, T):
 
 class OracleSim:
     """One FP64 oracle simulation.  Keyword arguments mirror ``or_params`` in lbm_oracle.h;
-    for the Carnahan-Starling EOS pass either ``T`` or ``T_over_Tc``."""
+    for the Carnahan-Starling EOS pass either ``T`` or ``T_over_Tc``.  openmp: run it in the
+    -fopenmp build (same bits; threads from OMP_NUM_THREADS, else all host cores)."""
 
-    def __init__(self, nx, ny, tau, scheme=HBB, circles=(), T_over_Tc=None, **kw):
-        lib = _load()
+    def __init__(self, nx, ny, tau, scheme=HBB, circles=(), T_over_Tc=None, openmp=False, **kw):
+        lib = _load(openmp)
         if T_over_Tc is not None:
             Tc, _ = cs_critical(kw.get("a", 0.25), kw.get("b", 4.0), kw.get("R", 1.0))
             kw["T"] = T_over_Tc * Tc

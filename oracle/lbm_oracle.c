@@ -6,13 +6,19 @@
  * stage:  f (pre-collision) -> rho, psi, F, u -> f* (post-collision) -> f_new (streamed) ->
  * curved-wall schemes at the boundary nodes -> f_new becomes f.
  * No blocking, fusion or reordering beyond what the equations state.  Compile with
- * -O2 -ffp-contract=off (no fused multiply-add, no fast-math).
+ * -O2 -ffp-contract=off (no fused multiply-add, no fast-math).  The per-node loops carry OpenMP
+ * pragmas (ignored without -fopenmp): each node's arithmetic is the same in either build, every
+ * value is written by one iteration, and the ledger, the wall pass and the set-up stay serial,
+ * so the multi-threaded build gives the same bits.
  */
 #include "lbm_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* D2Q9 lattice, Sec. 2.1 below Eq. (4). */
 static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -390,6 +396,7 @@ void or_init_droplet(or_sim* s, double cx, double cy, double R, double W, double
 static void compute_macros(or_sim* s) {
   int nx = s->nx, ny = s->ny, N = s->N;
   const double* f = s->f;
+#pragma omp parallel for
   for (int n = 0; n < N; ++n) {
     if (s->solid[n]) { s->rho[n] = 0.0; continue; }
     double r = 0.0;
@@ -398,7 +405,9 @@ static void compute_macros(or_sim* s) {
   }
   int multiphase = s->p.eos != OR_EOS_NONE;
   double psi_w = multiphase ? or_psi(&s->p, s->p.rho_wall) : 0.0;
+#pragma omp parallel for
   for (int n = 0; n < N; ++n) s->psi[n] = s->solid[n] ? psi_w : (multiphase ? or_psi(&s->p, s->rho[n]) : 0.0);
+#pragma omp parallel for
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       int n = j * nx + i;
@@ -425,6 +434,7 @@ static void compute_macros(or_sim* s) {
       s->Fx[n] = Fx;
       s->Fy[n] = Fy;
     }
+#pragma omp parallel for
   for (int n = 0; n < N; ++n) {
     if (s->solid[n]) { s->ux[n] = s->uy[n] = 0.0; continue; }
     double mx = 0.0, my = 0.0;
@@ -626,6 +636,7 @@ void or_step(or_sim* s, int nsteps) {
   for (int step = 0; step < nsteps; ++step) {
     compute_macros(s);
     /* collision, Eq. (2) */
+#pragma omp parallel for
     for (int n = 0; n < N; ++n) {
       if (s->solid[n]) continue;
       double feq[9], fa[9];
@@ -638,6 +649,7 @@ void or_step(or_sim* s, int nsteps) {
     }
     /* streaming, Eq. (3); populations that would enter a solid node leave the fluid */
     memset(s->fn, 0, sizeof(double) * 9 * NN);
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         int n = j * nx + i;
@@ -694,3 +706,10 @@ void or_force(const or_sim* s, double* fx, double* fy) {
 }
 double or_last_max_node_leak(const or_sim* s) { return s->last_max_node_leak; }
 long or_fallbacks(const or_sim* s) { return s->fallbacks; }
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
