@@ -295,8 +295,8 @@ typedef struct {
 } lbm_tune_trial;
 
 /* opt: stream and allocation hook for the batch and every lattice in it (precision is taken
- * from the argument).  Starts with 16-row tiles and LBM_SCHED_CLAIM (lbm_batch_tune,
- * lbm_batch_set_schedule change them).  LBM_EINVAL for bad arguments. */
+ * from the argument).  Starts with 32-row tiles (FP64: 16) and LBM_SCHED_CLAIM
+ * (lbm_batch_tune, lbm_batch_set_schedule change them).  LBM_EINVAL for bad arguments. */
 lbm_status lbm_batch_create(int32_t precision, int32_t eos_kind, int32_t max_domains,
                             const lbm_options* opt, lbm_batch** out);
 /* Create, initialise and add a lattice with a budget of `steps` time steps; *slot receives its

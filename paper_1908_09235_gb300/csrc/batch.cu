@@ -242,7 +242,8 @@ lbm_status lbm_batch_create(int32_t precision, int32_t eos_kind, int32_t max_dom
   b->slots.assign(max_domains, nullptr);
   b->h_doms.assign(max_domains, BatchDomain{});
   b->uploaded.assign(max_domains, 0);
-  b->ry = 2;  // 16-row tiles, claimed: the fastest pair on the 512-lattice workload
+  // 32-row tiles (FP64: 16), claimed: the fastest pair on the 512-lattice workload
+  b->ry = precision == LBM_FP64 ? 2 : 4;
   b->sched = LBM_SCHED_CLAIM;
   b->step_grid = batch_step_grid(precision, eos_kind, b->ry);
   b->bnd_grid = 152 * 8;

@@ -19,8 +19,16 @@ namespace {
 
 using namespace step_core;
 
+// CTAs per SM the tile kernels are compiled for (register budget 65536 / (256 x this)), as
+// measured on the batched workload: FP32 storage, 3 for 32-row tiles (at 4 they spill; 5% slower)
+// and 4 for shorter ones; FP16 storage, 4 (at 3 its 32-row tiles ran 11% slower); FP64, 2.
+template <typename S, int RY>
+constexpr int tile_ctas() {
+  return sizeof(S) == 8 ? 2 : (sizeof(S) == 4 && RY == 4 ? 3 : 4);
+}
+
 template <typename S, int EOS, bool FIELDS>
-__global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(TX* TYT, tile_ctas<S, StoreTraits<S>::RY>())
     step_kernel(DevParams p, const void* __restrict__ fa, void* __restrict__ fb,
                 const uint8_t* __restrict__ flags, double* __restrict__ rho_m,
                 double* __restrict__ ux_m, double* __restrict__ uy_m) {
@@ -38,7 +46,7 @@ __global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 :
 // whose step budget is spent are skipped.  RY (rows per thread, so the tile height 8 RY) and the
 // queue are chosen by the batch's tuner.
 template <typename S, int EOS, int RY>
-__global__ void __launch_bounds__(TX* TYT, sizeof(typename Pop<S>::C) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(TX* TYT, tile_ctas<S, RY>())
     batch_step_kernel(const BatchDomain* __restrict__ doms, const int4* __restrict__ tiles,
                       const int* __restrict__ n_tiles, int* __restrict__ claim) {
   using C = typename StoreTraits<S>::C;

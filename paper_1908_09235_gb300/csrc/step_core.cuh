@@ -27,13 +27,20 @@ __device__ __forceinline__ C pop_sum(const C (&f)[9]) {
   return r;
 }
 
-// A post-collision value rounded to the storage format of plane a (per element).
+// A post-collision value rounded to the storage format of plane a (per element).  Node pairs of
+// the FP16 format round both elements in one paired conversion each way (round to nearest even
+// per element, the same values as one at a time).
 template <typename S, typename L>
 __device__ __forceinline__ L round_st(int a, L v) {
-  if constexpr (Elem<L>::W == 2)
-    return make_float2(Pop<S>::rounded(a, v.x), Pop<S>::rounded(a, v.y));
-  else
+  if constexpr (Elem<L>::W == 2) {
+    if constexpr (sizeof(S) == 2) {
+      return a == 0 ? v : __half22float2(__float22half2_rn(v));
+    } else {
+      return make_float2(Pop<S>::rounded(a, v.x), Pop<S>::rounded(a, v.y));
+    }
+  } else {
     return Pop<S>::rounded(a, v);
+  }
 }
 
 // The arithmetic of one fluid node (x, y), or of two nodes at once when L is float2 (the paired
