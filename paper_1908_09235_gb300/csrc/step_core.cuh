@@ -229,17 +229,19 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
   const C psi_w = k.psi_wall;
 
   // ---- phase 1: own nodes' populations, density and psi; psi of the ring ----
+  // In a ragged tile only the first column (row) past the lattice's edge is needed: it holds
+  // column 0 (row 0), the periodic neighbour of the last one.  Slots beyond it load nothing.
   const int x = x0 + tx;
-  const int xo = x < nx ? x : (small ? wrap_any(x, nx) : x - nx);
+  const int xo = x < nx ? x : 0;
   C f[RY][9];
   C rho[RY];
   uint8_t fl[RY];
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
     const int y = y0 + ty + r * TYT;
-    const int yo = y < ny ? y : (small ? wrap_any(y, ny) : y - ny);
+    const int yo = y < ny ? y : 0;
     const int n = yo * nx + xo;
-    fl[r] = flags[n];
+    fl[r] = (x <= nx && y <= ny) ? flags[n] : uint8_t(FLAG_SOLID);
     rho[r] = C(1);
     if (!(fl[r] & FLAG_SOLID)) {
 #pragma unroll
@@ -269,6 +271,7 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
         hy = (kk < TH ? kk : kk - TH) + 1;
       }
       int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+      const bool ring_need = gx <= nx && gy <= ny;  // past the first wrapped column: unused
       if (small) {
         gx = wrap_any(gx, nx);
         gy = wrap_any(gy, ny);
@@ -277,7 +280,7 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
         gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
       }
       const int m = gy * nx + gx;
-      ring_fluid = !(flags[m] & FLAG_SOLID);
+      ring_fluid = ring_need && !(flags[m] & FLAG_SOLID);
       if (ring_fluid) {
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = Pop<S>::load(fa, a, N, m);
