@@ -131,6 +131,15 @@ static void fill(Consts<C>& k, const DevParams& p) {
   k.omega = C(p.omega);
   k.one_m_omega = C(1.0 - p.omega);
   k.K = C(3.0 * p.guo_pref);
+  const double w[2] = {1.0 / 9.0, 1.0 / 36.0};
+  for (int c = 0; c < 2; ++c) {
+    k.wo45[c] = C(w[c] * 4.5 * p.omega);
+    k.wo3[c] = C(w[c] * 3.0 * p.omega);
+    k.wK3[c] = C(w[c] * 9.0 * p.guo_pref);
+    k.wK[c] = C(w[c] * 3.0 * p.guo_pref);
+  }
+  k.gw1 = C(-p.G / 3.0);
+  k.gw5 = C(-p.G / 12.0);
   k.G = C(p.G);
   k.psi0 = C(p.psi0);
   k.rho0 = C(p.rho0);

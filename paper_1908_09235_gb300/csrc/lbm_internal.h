@@ -23,6 +23,10 @@ enum : uint8_t {
 template <typename C>
 struct Consts {
   C omega, one_m_omega, K;     // 1/tau, 1 - 1/tau, 3 (1 - 1/(2 tau))
+  // FP64 collision coefficients per weight class c (0: axis, w = 1/9; 1: diagonal, w = 1/36):
+  // w 4.5 omega, w 3 omega, w 3 K, w K; and the force weights with -G folded in: -G/3, -G/12
+  C wo45[2], wo3[2], wK3[2], wK[2];
+  C gw1, gw5;
   C G, psi0, rho0, a, b4, RT, two_over_G, psi_wall;
   C gx, gy, azC, azcx, azcy;
   C rho_ref;

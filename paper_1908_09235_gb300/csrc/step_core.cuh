@@ -27,6 +27,16 @@ __device__ __forceinline__ C pop_sum(const C (&f)[9]) {
   return r;
 }
 
+// A node's density from its nine stored values: their sum, plus rho_ref for the deviation
+// formats (FP64 storage holds the populations themselves).
+template <bool DEV, typename L>
+__device__ __forceinline__ L density_of(typename Elem<L>::C rho_ref, const L (&f)[9]) {
+  if constexpr (DEV)
+    return r_add(splat<L>(rho_ref), pop_sum<L>(f));
+  else
+    return pop_sum<L>(f);
+}
+
 // A post-collision value rounded to the storage format of plane a (per element).  Node pairs of
 // the FP16 format round both elements in one paired conversion each way (round to nearest even
 // per element, the same values as one at a time).
@@ -60,17 +70,23 @@ __device__ __forceinline__ void collide_node(const DevParams& p,
   using C = typename Pop<S>::C;
   constexpr bool DEV = Pop<S>::dev;
   auto c_ = [](C v) { return splat<L>(v); };
-  const L rho_ref = c_(DEV ? k.rho_ref : C(0));
   L Fx = c_(C(0)), Fy = c_(C(0));
   if constexpr (EOS != LBM_EOS_NONE) {
     // -G psi(x) sum_a w_a psi(x + e_a) e_a, as weighted differences of opposite neighbours (the
     // subtractions of nearly equal psi are exact, which keeps FP32 forces accurate in smooth
-    // regions)
-    const L sx = r_fma(c_(wpsi<C>(1)), d13, r_mul(c_(wpsi<C>(5)), r_add(d57, d86)));
-    const L sy = r_fma(c_(wpsi<C>(2)), d24, r_mul(c_(wpsi<C>(5)), r_sub(d57, d86)));
-    const L mg = r_mul(c_(-k.G), psic);
-    Fx = r_mul(mg, sx);
-    Fy = r_mul(mg, sy);
+    // regions).  FP64: -G folded into the weights (gw1 = -G/3, gw5 = -G/12), one operation less.
+    if constexpr (sizeof(C) == 8) {
+      const L sx = r_fma(c_(k.gw1), d13, r_mul(c_(k.gw5), r_add(d57, d86)));
+      const L sy = r_fma(c_(k.gw1), d24, r_mul(c_(k.gw5), r_sub(d57, d86)));
+      Fx = r_mul(psic, sx);
+      Fy = r_mul(psic, sy);
+    } else {
+      const L sx = r_fma(c_(wpsi<C>(1)), d13, r_mul(c_(wpsi<C>(5)), r_add(d57, d86)));
+      const L sy = r_fma(c_(wpsi<C>(2)), d24, r_mul(c_(wpsi<C>(5)), r_sub(d57, d86)));
+      const L mg = r_mul(c_(-k.G), psic);
+      Fx = r_mul(mg, sx);
+      Fy = r_mul(mg, sy);
+    }
   }
   if (p.has_body) {
     Fx = r_fma(rh, c_(k.gx), Fx);
@@ -92,28 +108,56 @@ __device__ __forceinline__ void collide_node(const DevParams& p,
   //   f_eq = w [c0 + rho eu (3 + 4.5 eu)],  c0 = rho (1 - 1.5 u.u) (less rho_ref if stored
   //   as a deviation), and Guo's term F_a = w [K eF (1 + 3 eu) - K u.F], K = 3 (1 - 1/2tau),
   //   eu = e_a.u, eF = e_a.F.
-  const L omega = c_(k.omega), one_m_omega = c_(k.one_m_omega), K = c_(k.K);
   const L uu = r_fma(ux, ux, r_mul(uy, uy));
-  const L c0 = r_fma(r_mul(c_(C(-1.5)), rh), uu, r_sub(rh, rho_ref));
+  L rd = rh;  // rho, less rho_ref for the deviation formats
+  if constexpr (DEV) rd = r_sub(rh, c_(k.rho_ref));
+  const L c0 = r_fma(r_mul(c_(C(-1.5)), rh), uu, rd);
   const L uF = r_fma(ux, Fx, r_mul(uy, Fy));
-  const L A0 = r_fma(omega, c0, r_mul(c_(-k.K), uF));
-  const L orho = r_mul(omega, rh);
-  // Opposite directions a, abar share |e.u| and |e.F|: h_a = P + Q, h_abar = P - Q with the
-  // even part P = A0 + (4.5 rho omega eu + 3 K eF) eu and the odd part Q = 3 rho omega eu + K eF.
+  const L A0 = r_fma(c_(k.omega), c0, r_mul(c_(-k.K), uF));
+  const L one_m_omega = c_(k.one_m_omega);
+  // Opposite directions a, abar share |e.u| and |e.F|: h_a = w (P + Q), h_abar = w (P - Q) with
+  // the even part P = A0 + (4.5 rho omega eu + 3 K eF) eu and the odd part Q = 3 rho omega eu +
+  // K eF.
   L out[9];
   out[0] = r_fma(one_m_omega, g[0], r_mul(c_(wgt<C>(0)), A0));
-  const L o45 = r_mul(c_(C(4.5)), orho), o3 = r_mul(c_(C(3)), orho), K3 = r_mul(c_(C(3)), K);
+  if constexpr (sizeof(C) == 8) {
+    // FP64 arithmetic is bound by the FP64 pipe: w is folded into coefficients per weight class
+    // c (axis, diagonal), al = w 4.5 omega rho, be = w 3 omega rho, Aw = w A0 and the constants
+    // w 3 K, w K, which saves two operations per direction pair.
+    L al[2], be[2], Aw[2];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int a = i == 0 ? 1 : (i == 1 ? 2 : (i == 2 ? 5 : 6)), ab = opposite(a);
-    // e_a = (1,0), (0,1), (1,1), (-1,1)
-    const L eu = i == 0 ? ux : (i == 1 ? uy : (i == 2 ? r_add(ux, uy) : r_sub(uy, ux)));
-    const L eF = i == 0 ? Fx : (i == 1 ? Fy : (i == 2 ? r_add(Fx, Fy) : r_sub(Fy, Fx)));
-    const L P = r_fma(r_fma(o45, eu, r_mul(K3, eF)), eu, A0);
-    const L Q = r_fma(o3, eu, r_mul(K, eF));
-    const L w = c_(wgt<C>(a));
-    out[a] = r_fma(one_m_omega, g[a], r_mul(w, r_add(P, Q)));
-    out[ab] = r_fma(one_m_omega, g[ab], r_mul(w, r_sub(P, Q)));
+    for (int c = 0; c < 2; ++c) {
+      al[c] = r_mul(c_(k.wo45[c]), rh);
+      be[c] = r_mul(c_(k.wo3[c]), rh);
+      Aw[c] = r_mul(c_(wgt<C>(c == 0 ? 1 : 5)), A0);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int a = i == 0 ? 1 : (i == 1 ? 2 : (i == 2 ? 5 : 6)), ab = opposite(a), c = i >> 1;
+      // e_a = (1,0), (0,1), (1,1), (-1,1)
+      const L eu = i == 0 ? ux : (i == 1 ? uy : (i == 2 ? r_add(ux, uy) : r_sub(uy, ux)));
+      const L eF = i == 0 ? Fx : (i == 1 ? Fy : (i == 2 ? r_add(Fx, Fy) : r_sub(Fy, Fx)));
+      const L wP = r_fma(r_fma(al[c], eu, r_mul(c_(k.wK3[c]), eF)), eu, Aw[c]);
+      const L wQ = r_fma(be[c], eu, r_mul(c_(k.wK[c]), eF));
+      out[a] = r_fma(one_m_omega, g[a], r_add(wP, wQ));
+      out[ab] = r_fma(one_m_omega, g[ab], r_sub(wP, wQ));
+    }
+  } else {
+    // FP32 arithmetic (issue- and register-bound kernels): fewer live values per node
+    const L orho = r_mul(c_(k.omega), rh);
+    const L o45 = r_mul(c_(C(4.5)), orho), o3 = r_mul(c_(C(3)), orho);
+    const L K = c_(k.K), K3 = r_mul(c_(C(3)), K);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int a = i == 0 ? 1 : (i == 1 ? 2 : (i == 2 ? 5 : 6)), ab = opposite(a);
+      const L eu = i == 0 ? ux : (i == 1 ? uy : (i == 2 ? r_add(ux, uy) : r_sub(uy, ux)));
+      const L eF = i == 0 ? Fx : (i == 1 ? Fy : (i == 2 ? r_add(Fx, Fy) : r_sub(Fy, Fx)));
+      const L P = r_fma(r_fma(o45, eu, r_mul(K3, eF)), eu, A0);
+      const L Q = r_fma(o3, eu, r_mul(K, eF));
+      const L w = c_(wgt<C>(a));
+      out[a] = r_fma(one_m_omega, g[a], r_mul(w, r_add(P, Q)));
+      out[ab] = r_fma(one_m_omega, g[ab], r_mul(w, r_sub(P, Q)));
+    }
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) st[a] = round_st<S>(a, out[a]);
@@ -288,15 +332,16 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
     }
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
-      if (!(fl[r] & FLAG_SOLID)) rho[r] = r_add(rho_ref, pop_sum<C>(f[r]));
+      if (!(fl[r] & FLAG_SOLID)) rho[r] = density_of<DEV>(rho_ref, f[r]);
       psi_s[ty + r * TYT + 1][tx + 1] = (fl[r] & FLAG_SOLID) ? psi_w : psi_of<C, EOS>(k, rho[r]);
     }
-    if (c < kRing) psi_s[hy][hx] = ring_fluid ? psi_of<C, EOS>(k, r_add(rho_ref, pop_sum<C>(v))) : psi_w;
+    if (c < kRing)
+      psi_s[hy][hx] = ring_fluid ? psi_of<C, EOS>(k, density_of<DEV>(rho_ref, v)) : psi_w;
     __syncthreads();
   } else {
 #pragma unroll
     for (int r = 0; r < RY; ++r)
-      if (!(fl[r] & FLAG_SOLID)) rho[r] = r_add(rho_ref, pop_sum<C>(f[r]));
+      if (!(fl[r] & FLAG_SOLID)) rho[r] = density_of<DEV>(rho_ref, f[r]);
   }
 
   tile_phase2<S, EOS, FIELDS, RY>(p, fb, rho_m, ux_m, uy_m, x0, y0, psi_s, f, rho, fl);

@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
   L rho[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
-    const L r = r_add(splat<L>(rho_ref), pop_sum<L>(f[q]));
+    const L r = density_of<DEV>(rho_ref, f[q]);
     C re[W];
 #pragma unroll
     for (int e = 0; e < W; ++e) re[e] = (fl[W * q + e] & FLAG_SOLID) ? C(1) : el(r, e);
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
         }
         psi_s[prow][pj(pcol)] = (nf & FLAG_SOLID)
                                 ? psi_w
-                                : psi_of<C, EOS>(k, r_add(rho_ref, pop_sum<C>(g)));
+                                : psi_of<C, EOS>(k, density_of<DEV>(rho_ref, g));
       }
     }
     __syncthreads();  // psi_s complete
