@@ -207,16 +207,17 @@ __device__ __forceinline__ L psi_of(const Consts<C>& k, L rho) {
   if constexpr (EOS == LBM_EOS_EXP) {
     return r_mul(splat<L>(k.psi0), q_exp(r_mul(splat<L>(C(-1)), q_div(splat<L>(k.rho0), rho))));
   } else if constexpr (EOS == LBM_EOS_CS) {
-    // p = rho R T (1 + eta + eta^2 - eta^3) / (1 - eta)^3 - a rho^2,  eta = b rho / 4
+    // p = rho R T (1 + eta + eta^2 - eta^3) / (1 - eta)^3 - a rho^2,  eta = b rho / 4, so
+    // p - rho/3 = rho [R T num / (1 - eta)^3 - a rho - 1/3] with the numerator in Horner form
+    // num = 1 + eta (1 + eta (1 - eta))
     const L one = splat<L>(C(1));
     const L eta = r_mul(splat<L>(k.b4), rho);
     const L om = r_sub(one, eta);
-    const L e2 = r_mul(eta, eta);
-    const L num = r_sub(r_add(r_add(one, eta), e2), r_mul(e2, eta));
+    const L num = r_fma(eta, r_fma(eta, om, one), one);
     const L om3 = r_mul(r_mul(om, om), om);
-    const L pr = r_sub(q_div(r_mul(r_mul(rho, splat<L>(k.RT)), num), om3),
-                       r_mul(r_mul(splat<L>(k.a), rho), rho));
-    return q_sqrt(r_mul(r_sub(pr, r_mul(rho, splat<L>(C(1.0 / 3.0)))), splat<L>(k.two_over_G)));
+    const L inner = r_fma(splat<L>(k.RT), q_div(num, om3),
+                          r_fma(splat<L>(-k.a), rho, splat<L>(C(-1.0 / 3.0))));
+    return q_sqrt(r_mul(r_mul(rho, splat<L>(k.two_over_G)), inner));
   } else {
     return splat<L>(C(0));
   }
