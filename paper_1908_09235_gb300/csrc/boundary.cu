@@ -204,7 +204,7 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
   const T* uxT = reinterpret_cast<const T*>(ux_m);
   const T* uyT = reinterpret_cast<const T*>(uy_m);
 
-  // round 1: node and link records
+  // first loads: node and link records
   int n = 0, l0 = 0, nl = 0;
   if (node_ok) {
     n = bnode[b];
@@ -234,7 +234,7 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
     ubx = uxT[n];
     uby = uyT[n];
   }
-  // round 2: lattice values (deviations d_ for the FP32 formats; f = d_ + w rho_ref)
+  // second loads: lattice values (deviations d_ for the FP32 formats; f = d_ + w rho_ref)
   const T w = wgt<T>(a);
   const T wr = w * rref;
   T fo_d = T(0), X1 = T(0), X2 = T(0), usx = T(0), usy = T(0);
