@@ -205,7 +205,8 @@ lbm_status lbm_links(lbm_ctx* ctx, int32_t* node, uint8_t* dir, double* q, int64
 lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
 
 /* Channel flow past solid bodies (Sec. 5.1, steady flow past a circular cylinder): from the next
- * step on (and with the force recorded for lbm_force), column i = 0 is a velocity inlet with the uniform profile (u_in, 0) imposed by Zou and
+ * step on (and with the force recorded for lbm_force), column i = 0 is a velocity inlet with
+ * the uniform profile (u_in, 0) imposed by Zou and
  * He's rule for the three populations entering from the left, and column i = nx - 1 is a
  * fully developed outlet (the three populations entering from the right are those of column
  * nx - 2).  y stays periodic.  Single-phase flows only (eos kind LBM_EOS_NONE: the psi stencil is
@@ -221,6 +222,25 @@ lbm_status lbm_set_inflow(lbm_ctx* ctx, double u_in);
  * LBM_ESTATE unless the context records the force (lbm_options.track_force or
  * lbm_set_inflow).  The drag coefficient of Sec. 5.1 is fx / (0.5 rho U0^2 D). */
 lbm_status lbm_force(lbm_ctx* ctx, double* fx, double* fy);
+
+/* ---- Checkpoint and resume ------------------------------------------------------------------
+ * (No counterpart in the paper: a server preempts lattices and resumes them later.)  A state
+ * blob holds everything the later steps of a lattice depend on: a header naming the lattice
+ * (nx, ny, precision, scheme, EOS kind, tau), the step count, rho_ref, the channel settings of
+ * lbm_set_inflow, then the current populations in the storage format (lattice layout, one
+ * lattice) and the FP64 rounding carry of each boundary node (zeros for FP64 storage).
+ * Restored into a context created with the same arguments, the run continues bit for bit. */
+/* Size in bytes of the state blob of this context. */
+lbm_status lbm_state_bytes(const lbm_ctx* ctx, int64_t* bytes);
+/* Write the state into the caller-owned host buffer of `bytes` bytes (at least
+ * lbm_state_bytes).  Blocks.  LBM_ESTATE before the first initialisation, LBM_EINVAL for a short
+ * buffer. */
+lbm_status lbm_save_state(lbm_ctx* ctx, void* buf, int64_t bytes);
+/* Replace the context's state (populations, carry, step count, rho_ref, channel settings) by a
+ * blob from lbm_save_state.  Blocks.  LBM_EINVAL when the blob is short, not a state blob, or
+ * names another lattice (size, precision, scheme, EOS kind, tau); LBM_ESTATE for a lattice that
+ * belongs to a batch (its state lives in the batch's tables). */
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* buf, int64_t bytes);
 
 /* Total mass of caller-owned device arrays without allocating any memory.  (This entry point
  * has no counterpart in the paper; it serves callers that cannot allocate device memory: a host

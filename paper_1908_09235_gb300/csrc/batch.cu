@@ -296,6 +296,7 @@ lbm_status lbm_batch_add(lbm_batch* b, const lbm_domain* d, int64_t steps, int32
   lbm_ctx* c = nullptr;
   lbm_status st = lbm_create(&d->geometry, &d->eos, d->tau, d->scheme, &b->opt, &c);
   if (st != LBM_OK) return st;
+  c->in_batch = true;
   if (d->init == 1)
     st = lbm_init_droplet(c, d->cx, d->cy, d->R, d->W, d->rho_in, d->rho_out);
   else {

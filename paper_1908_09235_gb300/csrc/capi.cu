@@ -637,4 +637,100 @@ lbm_status lbm_force(lbm_ctx* c, double* fx, double* fy) {
   return LBM_OK;
 }
 
+namespace {
+
+// Header of a state blob (lbm_save_state); the populations and the carry follow it.
+struct StateHeader {
+  char magic[8];  // "LBMSTAT1"
+  int32_t nx, ny, precision, scheme, eos_kind, open_x;
+  double tau, rho_ref, u_in;
+  int64_t steps, lattice_bytes, nb;
+};
+constexpr char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+
+int64_t state_bytes(const lbm_ctx* c) {
+  return (int64_t)sizeof(StateHeader) + (int64_t)c->lattice_bytes + 8 * (int64_t)c->nb;
+}
+
+}  // namespace
+
+lbm_status lbm_state_bytes(const lbm_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return LBM_EINVAL;
+  *bytes = state_bytes(c);
+  return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_ctx* c, void* buf, int64_t bytes) {
+  if (!c || !buf) return LBM_EINVAL;
+  if (c->status) return c->status;
+  if (!c->initialized) return fail(c, LBM_ESTATE, "lbm_save_state before any initialisation");
+  if (bytes < state_bytes(c)) return fail(c, LBM_EINVAL, "state buffer too small");
+  StateHeader h{};
+  std::memcpy(h.magic, kStateMagic, 8);
+  h.nx = c->p.nx;
+  h.ny = c->p.ny;
+  h.precision = c->precision;
+  h.scheme = c->p.scheme;
+  h.eos_kind = c->p.eos;
+  h.open_x = c->open_x ? 1 : 0;
+  h.tau = c->p.tau;
+  h.rho_ref = c->p.rho_ref;
+  h.u_in = c->u_in;
+  h.steps = c->steps;
+  h.lattice_bytes = (int64_t)c->lattice_bytes;
+  h.nb = c->nb;
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  std::memcpy(out, &h, sizeof(h));
+  LBM_CUDA(c, cudaMemcpyAsync(out + sizeof(h), c->f[c->cur], c->lattice_bytes,
+                              cudaMemcpyDeviceToHost, c->stream));
+  if (c->nb > 0)
+    LBM_CUDA(c, cudaMemcpyAsync(out + sizeof(h) + c->lattice_bytes, c->carry, 8 * c->nb,
+                                cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* c, const void* buf, int64_t bytes) {
+  if (!c || !buf) return LBM_EINVAL;
+  if (c->status) return c->status;
+  if (c->in_batch)
+    return fail(c, LBM_ESTATE, "lbm_load_state on a lattice that belongs to a batch");
+  if (bytes < (int64_t)sizeof(StateHeader)) return fail(c, LBM_EINVAL, "state blob too short");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.nx != c->p.nx || h.ny != c->p.ny ||
+      h.precision != c->precision || h.scheme != c->p.scheme || h.eos_kind != c->p.eos ||
+      std::memcmp(&h.tau, &c->p.tau, sizeof(double)) != 0 ||
+      h.lattice_bytes != (int64_t)c->lattice_bytes || h.nb != c->nb || h.steps < 0 ||
+      bytes < state_bytes(c))
+    return fail(c, LBM_EINVAL, "not a state blob of this lattice");
+  if (h.open_x && (!std::isfinite(h.u_in) || std::fabs(h.u_in) >= 0.5))
+    return fail(c, LBM_EINVAL, "state blob with an invalid inflow velocity");
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  LBM_CUDA(c, cudaMemcpyAsync(c->f[0], in + sizeof(h), c->lattice_bytes, cudaMemcpyHostToDevice,
+                              c->stream));
+  LBM_CUDA(c, cudaMemsetAsync(c->f[1], 0, c->lattice_bytes, c->stream));
+  if (c->nb > 0)
+    LBM_CUDA(c, cudaMemcpyAsync(c->carry, in + sizeof(h) + c->lattice_bytes, 8 * c->nb,
+                                cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  const bool open_changed = (h.open_x != 0) != c->open_x;
+  c->p.rho_ref = h.rho_ref;
+  finalize_consts(c->p);
+  // captured steps hold the kernel parameters by value and the channel pass or not
+  if (c->p.rho_ref != c->graph_rho_ref || open_changed)
+    for (int k = 0; k < 2; ++k)
+      if (c->graph[k]) {
+        cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+      }
+  c->open_x = h.open_x != 0;
+  c->u_in = h.u_in;
+  if (c->open_x) c->track_force = true;
+  c->cur = 0;
+  c->steps = h.steps;
+  c->initialized = true;
+  return LBM_OK;
+}
+
 }  // extern "C"

@@ -243,6 +243,7 @@ struct lbm_ctx {
   bool rho_ref_auto = false;  // deviation storage: take rho_ref from the initial state
   bool use_tma = false;       // step kernel with TMA halo staging (step_tma.cu)
   int kernel_path = 0;        // lbm_options.kernel_path
+  bool in_batch = false;      // owned by a batch (lbm_batch_add)
   alignas(64) unsigned char tmap[2][128];  // tensor maps of the two lattices
   alignas(64) unsigned char fmap[128];     // tensor map of the node flags
 };

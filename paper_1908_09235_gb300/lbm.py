@@ -33,7 +33,8 @@ EXPORTS = ("lbm_create", "lbm_coexistence", "lbm_init_fields", "lbm_init_droplet
            "lbm_batch_set_steps", "lbm_batch_step", "lbm_batch_step_timed", "lbm_batch_progress",
            "lbm_batch_domain", "lbm_batch_tune", "lbm_batch_info", "lbm_domain_bytes",
            "lbm_batch_last_error", "lbm_batch_destroy", "lbm_batch_poll", "lbm_set_inflow",
-           "lbm_force", "lbm_batch_tune_trials", "lbm_batch_set_schedule")
+           "lbm_force", "lbm_batch_tune_trials", "lbm_batch_set_schedule", "lbm_state_bytes",
+           "lbm_save_state", "lbm_load_state")
 
 # lbm_schedule: how the CTAs of a batch's step kernel take tiles from its queue
 SCHED_STRIDED, SCHED_CLAIM, SCHED_CLAIM_LARGEST_FIRST = 0, 1, 2
@@ -157,6 +158,9 @@ def load_library(build_if_missing=True):
             "lbm_batch_tune_trials": (C.c_int, [P, C.c_int32, C.POINTER(TuneTrial),
                                                 C.POINTER(C.c_int32)]),
             "lbm_batch_set_schedule": (C.c_int, [P, C.c_int32, C.c_int32]),
+            "lbm_state_bytes": (C.c_int, [P, C.POINTER(C.c_int64)]),
+            "lbm_save_state": (C.c_int, [P, C.c_void_p, C.c_int64]),
+            "lbm_load_state": (C.c_int, [P, C.c_void_p, C.c_int64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -252,6 +256,22 @@ def lbm_force(ctx):
     fx, fy = C.c_double(), C.c_double()
     _check(ctx, load_library().lbm_force(ctx, C.byref(fx), C.byref(fy)))
     return fx.value, fy.value
+
+
+def lbm_save_state(ctx):
+    """The context's state blob (checkpoint) as a numpy uint8 array."""
+    import numpy as np
+    n = C.c_int64()
+    _check(ctx, load_library().lbm_state_bytes(ctx, C.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(ctx, load_library().lbm_save_state(ctx, buf.ctypes.data, n.value))
+    return buf
+
+
+def lbm_load_state(ctx, blob):
+    import numpy as np
+    buf = np.ascontiguousarray(blob, dtype=np.uint8)
+    _check(ctx, load_library().lbm_load_state(ctx, buf.ctypes.data, buf.size))
 
 
 def lbm_info(ctx):
@@ -398,6 +418,13 @@ class Lattice:
     def force(self):
         """Momentum-exchange force (fx, fy) on the solid nodes during the last step."""
         return lbm_force(self.ctx)
+
+    def save_state(self):
+        """Checkpoint: the state blob (numpy uint8) that load_state restores bit for bit."""
+        return lbm_save_state(self.ctx)
+
+    def load_state(self, blob):
+        lbm_load_state(self.ctx, blob)
 
 
 # ---- batches -------------------------------------------------------------------------------------
