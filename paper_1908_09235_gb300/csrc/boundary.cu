@@ -52,7 +52,8 @@ __global__ void link_setup_kernel(DevParams p, int nb, const int32_t* __restrict
     const int ns = wrap_once(j + ey(a), ny) * nx + wrap_once(i + ex(a), nx);
     const int nf = wrap_once(j - ey(a), ny) * nx + wrap_once(i - ex(a), nx);
     const int nff = wrap_once(j - 2 * ey(a), ny) * nx + wrap_once(i - 2 * ex(a), nx);
-    const bool f_solid = flags[nf] & FLAG_SOLID, ff_solid = flags[nff] & FLAG_SOLID;
+    const bool f_solid = flags[LBM_CHK(nf, N)] & FLAG_SOLID;
+    const bool ff_solid = flags[LBM_CHK(nff, N)] & FLAG_SOLID;
     double c0 = 1.0, c1 = 0.0, c2 = 0.0, chi = 0.0, cus = 0.0;  // default: halfway bounce-back
     int x1 = -1, x2 = -1, uf = -1;
     uint8_t kind = 0;
@@ -230,7 +231,7 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
     c2 = pick<T>(r.c2, r.c2f, l);
     chi = pick<T>(r.chi, r.chif, l);
     cus = pick<T>(r.cus, r.cusf, l);
-    rho_b = rhoT[n];
+    rho_b = rhoT[LBM_CHK(n, N)];
     ubx = uxT[n];
     uby = uyT[n];
   }
@@ -244,7 +245,7 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
     if (x2 >= 0) X2 = Pop<S>::load_t((kind & kFromA) ? L.src : L.dst, x2, N) + wr;
     if (kind & kGhost) {
       if (uf >= 0) {
-        usx = uxT[uf];
+        usx = uxT[LBM_CHK(uf, N)];
         usy = uyT[uf];
       } else {
         usx = cus * ubx;

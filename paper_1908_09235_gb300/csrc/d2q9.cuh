@@ -7,6 +7,25 @@
 
 namespace lbm {
 
+// Index checks of the debug build (-DLBM_CHECKED, the library variant liblbm_gb300_checked.so):
+// an index outside [0, limit) is reported by device printf ("LBM_OOB <file>:<line> ...") and
+// replaced by 0, so the access stays inside the buffer and the run continues.  In the normal
+// build LBM_CHK(i, limit) is i.
+#ifdef LBM_CHECKED
+__device__ __noinline__ inline long long oob_report(long long i, long long limit,
+                                                    const char* file, int line) {
+  printf("LBM_OOB %s:%d index %lld limit %lld\n", file, line, i, limit);
+  return 0;
+}
+#define LBM_CHK(i, limit)                                                             \
+  ((long long)(i) >= 0 && (long long)(i) < (long long)(limit)                          \
+       ? (i)                                                                            \
+       : static_cast<decltype(i)>(oob_report((long long)(i), (long long)(limit), __FILE__, \
+                                             __LINE__)))
+#else
+#define LBM_CHK(i, limit) (i)
+#endif
+
 // Directions 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
 __host__ __device__ constexpr int ex(int a) {
   return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0);
@@ -48,25 +67,25 @@ struct Pop<double> {
   using C = double;
   static constexpr bool dev = false;
   static __device__ __forceinline__ C load(const void* b, int a, int N, int n) {
-    return static_cast<const double*>(b)[a * N + n];
+    return static_cast<const double*>(b)[a * N + LBM_CHK(n, N)];
   }
   static __device__ __forceinline__ C rounded(int a, C v) { return v; }
   static __device__ __forceinline__ void store(void* b, int a, int N, int n, C v) {
-    static_cast<double*>(b)[a * N + n] = v;
+    static_cast<double*>(b)[a * N + LBM_CHK(n, N)] = v;
   }
   // element e = a N + n, in the arithmetic type C; store_t returns the value as stored
   static __device__ __forceinline__ C load_t(const void* b, int e, int N) {
-    return static_cast<const double*>(b)[e];
+    return static_cast<const double*>(b)[LBM_CHK(e, 9 * N)];
   }
   static __device__ __forceinline__ C store_t(void* b, int e, int N, C v) {
-    static_cast<double*>(b)[e] = v;
+    static_cast<double*>(b)[LBM_CHK(e, 9 * N)] = v;
     return v;
   }
   static __device__ __forceinline__ double load_e(const void* b, int e, int N) {
-    return static_cast<const double*>(b)[e];
+    return static_cast<const double*>(b)[LBM_CHK(e, 9 * N)];
   }
   static __device__ __forceinline__ double store_e(void* b, int e, int N, double v) {
-    static_cast<double*>(b)[e] = v;
+    static_cast<double*>(b)[LBM_CHK(e, 9 * N)] = v;
     return v;
   }
 };
@@ -75,25 +94,25 @@ struct Pop<float> {
   using C = float;
   static constexpr bool dev = true;
   static __device__ __forceinline__ C load(const void* b, int a, int N, int n) {
-    return static_cast<const float*>(b)[a * N + n];
+    return static_cast<const float*>(b)[a * N + LBM_CHK(n, N)];
   }
   static __device__ __forceinline__ C rounded(int a, C v) { return v; }
   static __device__ __forceinline__ void store(void* b, int a, int N, int n, C v) {
-    static_cast<float*>(b)[a * N + n] = v;
+    static_cast<float*>(b)[a * N + LBM_CHK(n, N)] = v;
   }
   static __device__ __forceinline__ C load_t(const void* b, int e, int N) {
-    return static_cast<const float*>(b)[e];
+    return static_cast<const float*>(b)[LBM_CHK(e, 9 * N)];
   }
   static __device__ __forceinline__ C store_t(void* b, int e, int N, C v) {
-    static_cast<float*>(b)[e] = v;
+    static_cast<float*>(b)[LBM_CHK(e, 9 * N)] = v;
     return v;
   }
   static __device__ __forceinline__ double load_e(const void* b, int e, int N) {
-    return double(static_cast<const float*>(b)[e]);
+    return double(static_cast<const float*>(b)[LBM_CHK(e, 9 * N)]);
   }
   static __device__ __forceinline__ double store_e(void* b, int e, int N, double v) {
     const float s = float(v);
-    static_cast<float*>(b)[e] = s;
+    static_cast<float*>(b)[LBM_CHK(e, 9 * N)] = s;
     return double(s);
   }
 };
@@ -108,21 +127,25 @@ struct Pop<__half> {
     return reinterpret_cast<__half*>(static_cast<float*>(b) + N);
   }
   static __device__ __forceinline__ C load(const void* b, int a, int N, int n) {
+    n = LBM_CHK(n, N);
     return a == 0 ? static_cast<const float*>(b)[n] : __half2float(moving(b, N)[(a - 1) * N + n]);
   }
   static __device__ __forceinline__ C rounded(int a, C v) {
     return a == 0 ? v : __half2float(__float2half_rn(v));
   }
   static __device__ __forceinline__ void store(void* b, int a, int N, int n, C v) {
+    n = LBM_CHK(n, N);
     if (a == 0)
       static_cast<float*>(b)[n] = v;
     else
       moving(b, N)[(a - 1) * N + n] = __float2half_rn(v);
   }
   static __device__ __forceinline__ C load_t(const void* b, int e, int N) {
+    e = LBM_CHK(e, 9 * N);
     return e < N ? static_cast<const float*>(b)[e] : __half2float(moving(b, N)[e - N]);
   }
   static __device__ __forceinline__ C store_t(void* b, int e, int N, C v) {
+    e = LBM_CHK(e, 9 * N);
     if (e < N) {
       static_cast<float*>(b)[e] = v;
       return v;
@@ -132,10 +155,12 @@ struct Pop<__half> {
     return __half2float(h);
   }
   static __device__ __forceinline__ double load_e(const void* b, int e, int N) {
+    e = LBM_CHK(e, 9 * N);
     return e < N ? double(static_cast<const float*>(b)[e])
                  : double(__half2float(moving(b, N)[e - N]));
   }
   static __device__ __forceinline__ double store_e(void* b, int e, int N, double v) {
+    e = LBM_CHK(e, 9 * N);
     if (e < N) {
       const float s = float(v);
       static_cast<float*>(b)[e] = s;

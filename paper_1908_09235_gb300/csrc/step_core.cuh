@@ -200,7 +200,7 @@ __device__ __forceinline__ void tile_phase2(const DevParams& p, void* __restrict
   for (int r = 0; r < RY; ++r) {
     const int y = y0 + ty + r * TYN;
     if (x >= nx || y >= ny) continue;
-    const int n = y * nx + x;
+    const int n = LBM_CHK(y * nx + x, N);
     if (fl[r] & FLAG_SOLID) {
       if constexpr (FIELDS) {
         const double nan = __longlong_as_double(0x7ff8000000000000LL);
@@ -285,7 +285,7 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
     const int y = y0 + ty + r * TYT;
     const int yo = y < ny ? y : 0;
     const int n = yo * nx + xo;
-    fl[r] = (x <= nx && y <= ny) ? flags[n] : uint8_t(FLAG_SOLID);
+    fl[r] = (x <= nx && y <= ny) ? flags[LBM_CHK(n, N)] : uint8_t(FLAG_SOLID);
     rho[r] = C(1);
     if (!(fl[r] & FLAG_SOLID)) {
 #pragma unroll
@@ -324,7 +324,7 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
         gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
       }
       const int m = gy * nx + gx;
-      ring_fluid = ring_need && !(flags[m] & FLAG_SOLID);
+      ring_fluid = ring_need && !(flags[LBM_CHK(m, N)] & FLAG_SOLID);
       if (ring_fluid) {
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = Pop<S>::load(fa, a, N, m);

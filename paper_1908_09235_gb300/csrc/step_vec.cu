@@ -61,21 +61,22 @@ struct Vec<float> {
   static constexpr int ES = 4;  // largest element size in bytes
   static constexpr int kBlocks = 3;
   static __device__ __forceinline__ const float* at(const void* b, int a, int N, int n) {
-    return static_cast<const float*>(b) + a * N + n;
+    return static_cast<const float*>(b) + a * N + LBM_CHK(n, N - 3);
   }
   static __device__ __forceinline__ void load(const void* b, int a, int N, int n, float (&o)[4]) {
     const float4 v = __ldcg(reinterpret_cast<const float4*>(at(b, a, N, n)));
     o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
   }
   static __device__ __forceinline__ void store(void* b, int a, int N, int n, const float (&v)[4]) {
-    *reinterpret_cast<float4*>(static_cast<float*>(b) + a * N + n) =
+    *reinterpret_cast<float4*>(static_cast<float*>(b) + a * N + LBM_CHK(n, N - 3)) =
         make_float4(v[0], v[1], v[2], v[3]);
   }
   static __device__ __forceinline__ void store1(void* b, int a, int N, int n, float v) {
-    static_cast<float*>(b)[a * N + n] = v;
+    static_cast<float*>(b)[a * N + LBM_CHK(n, N)] = v;
   }
   static __device__ __forceinline__ void store2(void* b, int a, int N, int n, float v0, float v1) {
-    *reinterpret_cast<float2*>(static_cast<float*>(b) + a * N + n) = make_float2(v0, v1);
+    *reinterpret_cast<float2*>(static_cast<float*>(b) + a * N + LBM_CHK(n, N - 1)) =
+        make_float2(v0, v1);
   }
   static __device__ __forceinline__ int bytes(int a) { return 16; }
   static __device__ __forceinline__ const void* src(const void* b, int a, int N, int n) {
@@ -92,7 +93,7 @@ struct Vec<double> {
   static constexpr int ES = 8;
   static constexpr int kBlocks = 2;
   static __device__ __forceinline__ const double* at(const void* b, int a, int N, int n) {
-    return static_cast<const double*>(b) + a * N + n;
+    return static_cast<const double*>(b) + a * N + LBM_CHK(n, N - 1);
   }
   static __device__ __forceinline__ void load(const void* b, int a, int N, int n,
                                               double (&o)[2]) {
@@ -101,14 +102,16 @@ struct Vec<double> {
   }
   static __device__ __forceinline__ void store(void* b, int a, int N, int n,
                                                const double (&v)[2]) {
-    *reinterpret_cast<double2*>(static_cast<double*>(b) + a * N + n) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(static_cast<double*>(b) + a * N + LBM_CHK(n, N - 1)) =
+        make_double2(v[0], v[1]);
   }
   static __device__ __forceinline__ void store1(void* b, int a, int N, int n, double v) {
-    static_cast<double*>(b)[a * N + n] = v;
+    static_cast<double*>(b)[a * N + LBM_CHK(n, N)] = v;
   }
   static __device__ __forceinline__ void store2(void* b, int a, int N, int n, double v0,
                                                 double v1) {
-    *reinterpret_cast<double2*>(static_cast<double*>(b) + a * N + n) = make_double2(v0, v1);
+    *reinterpret_cast<double2*>(static_cast<double*>(b) + a * N + LBM_CHK(n, N - 1)) =
+        make_double2(v0, v1);
   }
   static __device__ __forceinline__ int bytes(int a) { return 16; }
   static __device__ __forceinline__ const void* src(const void* b, int a, int N, int n) {
@@ -125,9 +128,11 @@ struct Vec<__half> {
   static constexpr int ES = 4;
   static constexpr int kBlocks = 3;
   static __device__ __forceinline__ const __half* moving(const void* b, int a, int N, int n) {
-    return reinterpret_cast<const __half*>(static_cast<const float*>(b) + N) + (a - 1) * N + n;
+    return reinterpret_cast<const __half*>(static_cast<const float*>(b) + N) + (a - 1) * N +
+           LBM_CHK(n, N);
   }
   static __device__ __forceinline__ void load(const void* b, int a, int N, int n, float (&o)[4]) {
+    n = LBM_CHK(n, N - 3);
     if (a == 0) {
       const float4 v = __ldcg(reinterpret_cast<const float4*>(static_cast<const float*>(b) + n));
       o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
@@ -140,6 +145,7 @@ struct Vec<__half> {
   }
   // v already rounded to the storage format (Pop<__half>::rounded), so the conversion is exact
   static __device__ __forceinline__ void store(void* b, int a, int N, int n, const float (&v)[4]) {
+    n = LBM_CHK(n, N - 3);
     if (a == 0) {
       *reinterpret_cast<float4*>(static_cast<float*>(b) + n) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
@@ -155,10 +161,12 @@ struct Vec<__half> {
     *const_cast<__half*>(moving(b, a, N, n)) = __float2half_rn(v);
   }
   static __device__ __forceinline__ void store2(void* b, int a, int N, int n, float v0, float v1) {
-    *reinterpret_cast<__half2*>(const_cast<__half*>(moving(b, a, N, n))) = __floats2half2_rn(v0, v1);
+    *reinterpret_cast<__half2*>(const_cast<__half*>(moving(b, a, N, LBM_CHK(n, N - 1)))) =
+        __floats2half2_rn(v0, v1);
   }
   static __device__ __forceinline__ int bytes(int a) { return a == 0 ? 16 : 8; }
   static __device__ __forceinline__ const void* src(const void* b, int a, int N, int n) {
+    n = LBM_CHK(n, N - 3);
     return a == 0 ? static_cast<const void*>(static_cast<const float*>(b) + n)
                   : static_cast<const void*>(moving(b, a, N, n));
   }
@@ -269,13 +277,15 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int sl = lane + VW * h;
-          if (sl < nslot) cp_async4(ring_fl + r * SW + 4 * sl, flags + grow + wrapx(x0 + 4 * (sl - 1)));
+          if (sl < nslot)
+            cp_async4(ring_fl + r * SW + 4 * sl,
+                      flags + LBM_CHK(grow + wrapx(x0 + 4 * (sl - 1)), N - 3));
         }
       }
       if (lane == 18 || lane == 19) {
         const int side = lane - 18;
         cp_async4(side_fl + (w * 2 + side) * 4,
-                  flags + grow_w + wrapx(side == 0 ? x0 - 4 : x0 + 4 * nv));
+                  flags + LBM_CHK(grow_w + wrapx(side == 0 ? x0 - 4 : x0 + 4 * nv), N - 3));
       }
     } else {
 #pragma unroll
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
             gy = wrapy(y0 + (qq >> 1));
             gx = wrapx((qq & 1) == 0 ? x0 - 1 : x0 + V * nv);
           }
-          qfl[i] = flags[gy * nx + gx];
+          qfl[i] = flags[LBM_CHK(gy * nx + gx, N)];
         }
       }
     }
@@ -308,7 +318,7 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
   constexpr int W = Elem<L>::W, NP = V / W;
   L f[NP][9];
   uint8_t fl[V];
-  load_flags<V>(flags, n, fl);
+  load_flags<V>(flags, LBM_CHK(n, N - V + 1), fl);
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     C t[V];
@@ -330,7 +340,7 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
 #pragma unroll
       for (int e = 0; e < W; ++e)
         if (lane_ok)
-          psi_s[w + 1][pj(V * (lane + 1) + W * q + e)] =
+          psi_s[w + 1][LBM_CHK(pj(V * (lane + 1) + W * q + e), SWP)] =
               (fl[W * q + e] & FLAG_SOLID) ? psi_w : el(ps, e);
     }
   }
@@ -369,7 +379,7 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
           else
             nf = side_fl[((q - 2 * RJ) >> 1) * 8 + (((q - 2 * RJ) & 1) ? 4 : 0) + j];
         }
-        psi_s[prow][pj(pcol)] = (nf & FLAG_SOLID)
+        psi_s[LBM_CHK(prow, VH + 2)][LBM_CHK(pj(pcol), SWP)] = (nf & FLAG_SOLID)
                                 ? psi_w
                                 : psi_of<C, EOS>(k, density_of<DEV>(rho_ref, g));
       }
@@ -411,25 +421,25 @@ __global__ void __launch_bounds__(VW* VH, Vec<S>::kBlocks)
                             pack<L>(C(x), C(x + W - 1)), splat<L>(C(yo)), st, ux, uy);
 #pragma unroll
     for (int e = 0; e < W; ++e) {
-      const int nn = yo * nx + x + e;
+      const int nn = yo * nx + x + e;  // used by lanes inside the lattice only
       const uint8_t fe = fl[W * q + e];
       if constexpr (FIELDS) {
         if (lane_ok) {
           const double nan = __longlong_as_double(0x7ff8000000000000LL);
           const bool solid = fe & FLAG_SOLID;
-          rho_m[nn] = solid ? nan : double(el(rho[q], e));
-          ux_m[nn] = solid ? nan : double(el(ux, e));
-          uy_m[nn] = solid ? nan : double(el(uy, e));
+          rho_m[LBM_CHK(nn, N)] = solid ? nan : double(el(rho[q], e));
+          ux_m[LBM_CHK(nn, N)] = solid ? nan : double(el(ux, e));
+          uy_m[LBM_CHK(nn, N)] = solid ? nan : double(el(uy, e));
         }
       } else if (lane_ok && (fe & FLAG_MACRO)) {  // for the wall pass (fluid nodes only)
         if constexpr (DEV) {
-          reinterpret_cast<float*>(rho_m)[nn] = el(rho[q], e);
-          reinterpret_cast<float*>(ux_m)[nn] = el(ux, e);
-          reinterpret_cast<float*>(uy_m)[nn] = el(uy, e);
+          reinterpret_cast<float*>(rho_m)[LBM_CHK(nn, N)] = el(rho[q], e);
+          reinterpret_cast<float*>(ux_m)[LBM_CHK(nn, N)] = el(ux, e);
+          reinterpret_cast<float*>(uy_m)[LBM_CHK(nn, N)] = el(uy, e);
         } else {
-          rho_m[nn] = el(rho[q], e);
-          ux_m[nn] = el(ux, e);
-          uy_m[nn] = el(uy, e);
+          rho_m[LBM_CHK(nn, N)] = el(rho[q], e);
+          ux_m[LBM_CHK(nn, N)] = el(ux, e);
+          uy_m[LBM_CHK(nn, N)] = el(uy, e);
         }
       }
     }

@@ -104,7 +104,7 @@ _lock = threading.Lock()
 
 
 def library_path():
-    return _build.LIB
+    return _build.CHECKED_LIB if os.environ.get("LBM_GB300_CHECKED") == "1" else _build.LIB
 
 
 def load_library(build_if_missing=True):
@@ -113,7 +113,11 @@ def load_library(build_if_missing=True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build() if build_if_missing else _build.LIB
+        checked = os.environ.get("LBM_GB300_CHECKED") == "1"  # index-checking debug build
+        if build_if_missing:
+            path = _build.build(checked=checked)
+        else:
+            path = _build.CHECKED_LIB if checked else _build.LIB
         if not os.path.exists(path):
             raise RuntimeError("CUDA library %s is missing; run __graft_entry__.build()" % path)
         lib = C.CDLL(path)
