@@ -33,7 +33,10 @@ def _droplet(nx, ny, precision, path, scheme):
     rl, rv = lbm.lbm_coexistence(eos)
     eos.rho_wall = rv
     r = max(1.0, 0.15 * min(nx, ny))
-    lat = lbm.Lattice(nx, ny, 1.0, scheme, circles=[(nx / 2 + 0.3, 0.35 * ny + 0.2, r)], eos=eos,
+    cx, cy = nx / 2 + 0.3, 0.35 * ny + 0.2
+    # a cylinder where it clears the periodic seam (lbm_create's rule), else none
+    fits = cx - r - 2 >= 0 and cx + r + 2 <= nx - 1 and cy - r - 2 >= 0 and cy + r + 2 <= ny - 1
+    lat = lbm.Lattice(nx, ny, 1.0, scheme, circles=[(cx, cy, r)] if fits else [], eos=eos,
                       precision=precision, kernel_path=path)
     lat.init_droplet(nx / 2, 0.35 * ny + r, max(1.0, 0.2 * min(nx, ny)), 4.0, rl, rv)
     return lat
