@@ -349,7 +349,7 @@ class Lattice:
 
     def __init__(self, nx, ny, tau, scheme=HBB, circles=(), wall_q_lo=0.0, wall_q_hi=0.0,
                  eos=None, precision=FP64, stream=None, torch_memory=True, graph_steps=0,
-                 rho_ref=0.0, kernel_path=0, track_force=False):
+                 rho_ref=0.0, kernel_path=0, track_force=False, memory=None):
         self.nx, self.ny = int(nx), int(ny)
         if isinstance(scheme, str):
             scheme = SCHEMES[scheme]
@@ -369,8 +369,8 @@ class Lattice:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         opt.stream = C.c_void_p(int(stream))
-        if torch_memory:
-            self.mem = TorchDeviceMemory()
+        if memory is not None or torch_memory:  # memory: an allocation hook like TorchDeviceMemory
+            self.mem = memory if memory is not None else TorchDeviceMemory()
             opt.alloc = self.mem.alloc_fn
             opt.free = self.mem.free_fn
         self.options = opt
@@ -465,7 +465,7 @@ class Batch:
     Device memory comes from PyTorch's allocator unless torch_memory is False."""
 
     def __init__(self, precision=FP64, eos_kind=EOS_CS, max_domains=64, stream=None,
-                 torch_memory=True):
+                 torch_memory=True, memory=None):
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         lib = load_library()
@@ -476,8 +476,8 @@ class Batch:
             stream = torch.cuda.current_stream().cuda_stream
         opt.stream = C.c_void_p(int(stream))
         self.mem = None
-        if torch_memory:
-            self.mem = TorchDeviceMemory()
+        if memory is not None or torch_memory:  # memory: an allocation hook like TorchDeviceMemory
+            self.mem = memory if memory is not None else TorchDeviceMemory()
             opt.alloc = self.mem.alloc_fn
             opt.free = self.mem.free_fn
         self.options = opt
