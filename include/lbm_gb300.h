@@ -242,6 +242,16 @@ lbm_status lbm_save_state(lbm_ctx* ctx, void* buf, int64_t bytes);
  * belongs to a batch (its state lives in the batch's tables). */
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* buf, int64_t bytes);
 
+/* Self-test of the bounded device waits (those of the TMA-staged step kernel, which give up
+ * after a time limit and report LBM_ETIMEOUT instead of hanging): one CTA waits on an mbarrier
+ * phase for at most limit_ns nanoseconds (1 .. 1e10).  complete != 0: an arrival completes the
+ * phase first; the call returns LBM_OK with *completed = 1.  complete = 0: nothing completes
+ * it, the wait gives up after limit_ns; the call returns LBM_ETIMEOUT with *completed = 0.  The
+ * device stays usable either way.  stream: a cudaStream_t or NULL.  Blocks.  Needs no context;
+ * LBM_EINVAL for a limit out of range. */
+lbm_status lbm_selftest_bounded_wait(int64_t limit_ns, int32_t complete, void* stream,
+                                     int32_t* completed);
+
 /* Total mass of caller-owned device arrays without allocating any memory.  (This entry point
  * has no counterpart in the paper; it serves callers that cannot allocate device memory: a host
  * framework that already holds the device memory in its own pool, or a latency-critical loop

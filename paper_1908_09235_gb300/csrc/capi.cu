@@ -637,6 +637,28 @@ lbm_status lbm_force(lbm_ctx* c, double* fx, double* fy) {
   return LBM_OK;
 }
 
+lbm_status lbm_selftest_bounded_wait(int64_t limit_ns, int32_t complete, void* stream,
+                                     int32_t* completed) {
+  if (!completed || limit_ns <= 0 || limit_ns > 10000000000LL) return LBM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d = nullptr;
+  if (cudaMallocAsync(&d, sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  int h = -1;
+  cudaError_t e = launch_wait_selftest((unsigned long long)limit_ns, complete ? 1 : 0, d, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(d, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  *completed = h;
+  return h == 1 ? LBM_OK : LBM_ETIMEOUT;
+}
+
 namespace {
 
 // Header of a state blob (lbm_save_state); the populations and the carry follow it.

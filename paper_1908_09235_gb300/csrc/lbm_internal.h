@@ -183,6 +183,10 @@ cudaError_t launch_droplet_rho(const DevParams& p, double cx, double cy, double 
 
 // step_tma.cu
 bool tma_step_supported(int precision, int nx, int ny);
+// one CTA waits (bounded by limit_ns) on an mbarrier that completes only with arrive; out[0]
+// receives 1 if the wait saw it complete
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int arrive, int* out,
+                                 cudaStream_t s);
 bool make_lattice_tensor_map(void* map, const void* base, int nx, int ny);
 bool make_flags_tensor_map(void* map, const void* base, int nx, int ny);
 cudaError_t launch_step_tma(const void* map, const void* flag_map, const DevParams& p,

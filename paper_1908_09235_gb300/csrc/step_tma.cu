@@ -69,13 +69,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Bounded wait for the given phase of a stage's barrier; false after about kWaitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the given phase of a stage's barrier; false after about limit_ns (and after
+// 2^32 polls whatever the clock says).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (long long i = 0; i < (1LL << 32); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 0 && global_ns() - t0 > kWaitNs) return false;
+    if ((i & 63) == 0 && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -109,6 +111,22 @@ __device__ __forceinline__ void fence_mbar_init() {
 // A tile whose staged boxes lie inside the lattice (no periodic wrap): copied by TMA.
 __device__ __forceinline__ bool tma_tile(int x0, int y0, int nx, int ny) {
   return x0 >= 32 && x0 + 48 <= nx && y0 >= 1 && y0 + 33 <= ny;
+}
+
+// Self-test of the bounded wait: one CTA waits on phase 0 of a barrier that expects one arrival.
+// With arrive, thread 0 arrives and the phase completes; without, nothing completes it and the
+// wait must give up after limit_ns.  out[0]: 1 if the wait saw the phase complete, else 0.
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int arrive, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&bar)) : "memory");
+  const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+  if (threadIdx.x == 0) out[0] = ok ? 1 : 0;
 }
 
 template <int EOS>
@@ -292,6 +310,12 @@ cudaError_t launch_tma_t(const CUtensorMap& map, const CUtensorMap& fmap, const 
 }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int arrive, int* out,
+                                 cudaStream_t s) {
+  wait_selftest_kernel<<<1, 128, 0, s>>>(limit_ns, arrive, out);
+  return cudaGetLastError();
+}
 
 bool tma_step_supported(int precision, int nx, int ny) {
   return precision == LBM_FP32_DEV && nx % 16 == 0 && nx >= 64 && ny >= 64 &&

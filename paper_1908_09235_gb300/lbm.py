@@ -34,7 +34,7 @@ EXPORTS = ("lbm_create", "lbm_coexistence", "lbm_init_fields", "lbm_init_droplet
            "lbm_batch_domain", "lbm_batch_tune", "lbm_batch_info", "lbm_domain_bytes",
            "lbm_batch_last_error", "lbm_batch_destroy", "lbm_batch_poll", "lbm_set_inflow",
            "lbm_force", "lbm_batch_tune_trials", "lbm_batch_set_schedule", "lbm_state_bytes",
-           "lbm_save_state", "lbm_load_state")
+           "lbm_save_state", "lbm_load_state", "lbm_selftest_bounded_wait")
 
 # lbm_schedule: how the CTAs of a batch's step kernel take tiles from its queue
 SCHED_STRIDED, SCHED_CLAIM, SCHED_CLAIM_LARGEST_FIRST = 0, 1, 2
@@ -165,6 +165,8 @@ def load_library(build_if_missing=True):
             "lbm_state_bytes": (C.c_int, [P, C.POINTER(C.c_int64)]),
             "lbm_save_state": (C.c_int, [P, C.c_void_p, C.c_int64]),
             "lbm_load_state": (C.c_int, [P, C.c_void_p, C.c_int64]),
+            "lbm_selftest_bounded_wait": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p,
+                                                    C.POINTER(C.c_int32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -276,6 +278,18 @@ def lbm_load_state(ctx, blob):
     import numpy as np
     buf = np.ascontiguousarray(blob, dtype=np.uint8)
     _check(ctx, load_library().lbm_load_state(ctx, buf.ctypes.data, buf.size))
+
+
+def lbm_selftest_bounded_wait(limit_ns, complete, stream=None):
+    """(status, completed) of the bounded-wait self-test (status 5, LBM_ETIMEOUT, when the wait
+    gave up); see include/lbm_gb300.h."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    done = C.c_int32(-1)
+    st = load_library().lbm_selftest_bounded_wait(int(limit_ns), int(complete),
+                                                  C.c_void_p(int(stream)), C.byref(done))
+    return st, done.value
 
 
 def lbm_info(ctx):

@@ -1,7 +1,8 @@
-"""Host-side fault injection (no GPU fault): device allocations that fail at every point of
-lbm_create, of a lattice's first initialisation and of lbm_batch_add.  Each failure comes back as
-LBM_ENOMEM, every block allocated before it is returned, and nothing else breaks: the same
-calls succeed afterwards."""
+"""Failure detection without a GPU fault.  Host-side injection: device allocations that fail at
+every point of lbm_create, of a lattice's first initialisation and of lbm_batch_add; each
+failure comes back as LBM_ENOMEM, every block allocated before it is returned, and the same calls
+succeed afterwards.  On the GPU: a bounded wait on a barrier phase that nothing completes gives
+up after its limit and reports LBM_ETIMEOUT, and the device stays usable."""
 import ctypes as C
 
 import numpy as np
@@ -104,3 +105,21 @@ def test_allocation_failure_in_batch_add_leaves_the_batch_usable(gpu_lib):
     assert b.progress(s0) == (20, 0) and b.progress(s1) == (20, 0)
     b.close()
     assert not mem.live
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable(gpu_lib):
+    # the bounded mbarrier wait of the TMA-staged kernel, on a phase nothing completes
+    import time
+    t0 = time.perf_counter()
+    st, done = lbm.lbm_selftest_bounded_wait(200_000_000, 0)  # 0.2 s
+    dt = time.perf_counter() - t0
+    assert (st, done) == (5, 0)  # LBM_ETIMEOUT: the wait gave up
+    assert 0.19 < dt < 10.0
+    assert lbm.lbm_selftest_bounded_wait(200_000_000, 1) == (0, 1)  # completed phase
+    # the device and the library keep working
+    lat = lbm.Lattice(64, 32, 1.0, lbm.MOD_B, circles=[(20.0, 16.0, 5.0)],
+                      eos=lbm.make_eos(lbm.EOS_NONE), precision=lbm.FP32_DEV, kernel_path=2)
+    lat.init_fields(np.ones(64 * 32))
+    lat.step(5)
+    assert abs(lat.mass() / lat.info()["n_fluid"] - 1) < 1e-6
+    lat.close()
