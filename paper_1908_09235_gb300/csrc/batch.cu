@@ -246,7 +246,7 @@ lbm_status lbm_batch_create(int32_t precision, int32_t eos_kind, int32_t max_dom
   b->ry = precision == LBM_FP64 ? 2 : 4;
   b->sched = LBM_SCHED_CLAIM;
   b->step_grid = batch_step_grid(precision, eos_kind, b->ry);
-  b->bnd_grid = 152 * 8;
+  b->bnd_grid = batch_boundary_grid(precision);
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete b;

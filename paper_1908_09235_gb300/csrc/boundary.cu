@@ -460,6 +460,22 @@ cudaError_t launch_batch_boundary(int precision, const BatchDomain* doms, const 
   return cudaGetLastError();
 }
 
+int batch_boundary_grid(int precision) {
+  // every 8-lane group walks items one after the other, each a chain of dependent loads: fill
+  // the GPU with as many resident groups as it takes
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* fn = precision == LBM_FP32_DEV ? (const void*)batch_boundary_kernel<float>
+                   : precision == LBM_FP16_DEV ? (const void*)batch_boundary_kernel<__half>
+                                               : (const void*)batch_boundary_kernel<double>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 128, 0) != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    per = 8;
+  }
+  return sms * per;
+}
+
 cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, int* claim, cudaStream_t s) {
   if (n_doms <= 0) return cudaSuccess;
   batch_advance_kernel<<<(n_doms + 127) / 128, 128, 0, s>>>(doms, n_doms, claim);

@@ -164,6 +164,8 @@ cudaError_t launch_batch_step(int precision, int eos, int ry, const BatchDomain*
                               cudaStream_t s);
 cudaError_t launch_batch_boundary(int precision, const BatchDomain* doms, const int2* items,
                                   const int* n_items, int grid, cudaStream_t s);
+// persistent grid of the batch's wall pass: all the CTAs the GPU holds at once
+int batch_boundary_grid(int precision);
 // also resets the tile counter *claim for the next step
 cudaError_t launch_batch_advance(BatchDomain* doms, int n_doms, int* claim, cudaStream_t s);
 
