@@ -87,6 +87,27 @@ def test_droplet_on_cylinder_fp64_1000_steps(gpu_lib, scheme):
     lat.close()
 
 
+# ---- the modified schemes at other wettabilities (Sec. 4.2): wall densities between rho_V and
+# rho_L (partial and complete wetting; rho_V, non-wetting, is the case above) ------------------
+@pytest.mark.parametrize("frac", [0.5, 0.75])
+@pytest.mark.parametrize("scheme", [lbm.MOD_A, lbm.MOD_B])
+def test_droplet_wettability_fp64(gpu_lib, scheme, frac):
+    c = workloads.CS
+    Tc, _ = O.cs_critical(c["a"], c["b"], c["R"])
+    rl, rv = O.cs_coexistence(c["a"], c["b"], c["R"], c["T_over_Tc"] * Tc)
+    w = workloads.SMALL
+    case = Case(w.nx, w.ny, w.tau, "cs", circles=w.circles, init=("droplet",) + tuple(w.drop),
+                rho_wall=rv + frac * (rl - rv))
+    lat, s = case.gpu(scheme), case.oracle(scheme)
+    m0 = lat.mass()
+    lat.step(1000)
+    s.step(1000)
+    err = compare_fields(lat.fields(), s.fields())
+    assert max(err) <= TOL64, err
+    assert abs(lat.mass() / m0 - 1) < 1e-12
+    lat.close()
+
+
 # ---- exponential psi (the paper's Sec. 3.2 fluid) incl. Zhao-Yong and Filippova-Haenel ----------
 @pytest.mark.parametrize("scheme,tau", [(lbm.ZHAO_YONG, 0.95), (lbm.FH, 1.5), (lbm.MLS, 0.95),
                                         (lbm.BOUZIDI_Q, 0.95), (lbm.MOD_B, 0.95)])

@@ -160,6 +160,37 @@ def test_bao_differs_from_scheme_b():
     assert sa.last_max_node_leak > 1e-9
 
 
+# --- Sec. 4.2 (the droplet with the modified schemes at several contact angles) ---------------
+# The wettability comes from the virtual wall density rho_w (psi at solid nodes = psi(rho_w),
+# Sec. 3.2); the paper does not give the values behind its angles (reading r4), so three rho_w
+# between the coexistence densities stand in: the vapour density (non-wetting), the midpoint
+# (partial wetting) and three quarters of the way to the liquid (complete wetting).
+@pytest.mark.parametrize("scheme", [O.MOD_A, O.MOD_B])
+def test_modified_schemes_at_three_wettabilities(scheme):
+    T, rl, rv = _cs()
+    n = 100
+    wetted = []
+    for frac in (0.0, 0.5, 0.75):
+        s = O.OracleSim(n, n, 1.0, scheme=scheme, circles=[(n / 2, 0.35 * n, 0.15 * n)],
+                        eos=O.EOS_CS, G=-1.0, a=A_CS, b=B_CS, R=R_CS, T=T,
+                        rho_wall=rv + frac * (rl - rv))
+        s.init_droplet(n / 2, 0.5 * n, 0.2 * n, 5.0, rl, rv)
+        m0 = s.mass()
+        s.step(1500)
+        rho, ux, uy = s.fields()
+        # total mass kept to round-off at every wettability (the paper: 0.01% at most)
+        assert abs(s.mass() / m0 - 1) < 1e-12
+        assert s.last_max_node_leak < 1e-15
+        fluid = np.isfinite(rho)
+        assert np.max(np.hypot(ux, uy)[fluid]) < 0.05  # a stable droplet
+        bnd = (s.flags() & 2) != 0
+        wetted.append(float((rho[bnd] > 0.5 * (rl + rv)).mean()))
+    # a larger wall density wets more of the cylinder: none, part of it, all of it
+    assert wetted[0] == 0.0
+    assert 0.1 < wetted[1] < 0.9
+    assert wetted[2] == 1.0
+
+
 # --- Sec. 3.2 / Fig. 8: droplet on a cylinder, leakage ordering of the original schemes -------
 def test_droplet_on_cylinder_leakage_ordering():
     # Half-size version of the paper's 300x350 case (cylinder R = 70 at (150, 130), nu = 0.15,
