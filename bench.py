@@ -252,13 +252,16 @@ def run_e2e(w, steps):
     t0 = time.perf_counter()
     lbm._check(lat.ctx, lib.lbm_init_fields(lat.ctx, host[0].data_ptr(), host[1].data_ptr(),
                                             host[2].data_ptr()))
+    t1 = time.perf_counter()  # lbm_init_fields blocks (it reads rho_ref back)
     lbm._check(lat.ctx, lib.lbm_step(lat.ctx, steps))
     lbm._check(lat.ctx, lib.lbm_fields(lat.ctx, out[0].data_ptr(), out[1].data_ptr(),
                                        out[2].data_ptr()))
     dt = time.perf_counter() - t0
     info = lat.info()
     lat.close()
-    return info["n_fluid"] * steps / dt / 1e6, 24 * n / steps, 24 * n / steps
+    split = {"upload_and_init_ms": round(1e3 * (t1 - t0), 2),
+             "steps_and_download_ms": round(1e3 * (t0 + dt - t1), 2)}
+    return info["n_fluid"] * steps / dt / 1e6, 24 * n / steps, 24 * n / steps, split
 
 
 # Table 1 of the paper (Sec. 5.1): 2L/D, separation angle (degrees), drag coefficient
@@ -701,7 +704,7 @@ def main():
                 "hbm_frac_step_kernel": round(
                     n_fluid * vb / (s_ms / args.variant_steps * 1e-3) / 1e9 / peak, 3)}
 
-    e2e_value, h2d, d2h = run_e2e(w, args.steps)
+    e2e_value, h2d, d2h, e2e_split = run_e2e(w, args.steps)
     e2e_value = world * e2e_value
 
     cpu = None
@@ -739,7 +742,8 @@ def main():
             "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
-                    "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1)},
+                    "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1),
+                    "split": e2e_split},
             "cpu_baseline": cpu,
             "variants": variants,
             "mass_after": m_after,
