@@ -160,13 +160,13 @@ def barrier(world):
         dist.barrier()
 
 
-def make_lattice(w, scheme, precision, kernel_path=0):
+def make_lattice(w, scheme, precision, kernel_path=0, graph_steps=0):
     from paper_1908_09235_gb300 import lbm
     eos = lbm.make_eos(lbm.EOS_CS, **w.eos)
     rl, rv = lbm.lbm_coexistence(eos)
     eos.rho_wall = rv
     lat = lbm.Lattice(w.nx, w.ny, w.tau, scheme, circles=w.circles, eos=eos,
-                      precision=precision, kernel_path=kernel_path)
+                      precision=precision, kernel_path=kernel_path, graph_steps=graph_steps)
     lat.init_droplet(*w.drop, rl, rv)
     return lat, (rl, rv)
 
@@ -671,15 +671,26 @@ def main():
     from paper_1908_09235_gb300 import lbm
     lbm.load_library()
 
-    # ---- headline: scheme B, FP32 deviation storage ----
-    lat, _ = make_lattice(w, lbm.MOD_B, lbm.FP32_DEV)
-    lat.step_timed(args.warmup)
+    # ---- headline: scheme B, FP32 deviation storage, through lbm_step (the path a user
+    # takes): captured CUDA graphs of gs steps, which the warm-up builds and runs; CUDA events on
+    # the library's stream around the K timed steps ----
+    gs = max(2, min(32, args.warmup - args.warmup % 2))
+    lat, _ = make_lattice(w, lbm.MOD_B, lbm.FP32_DEV, graph_steps=gs)
+    lat.step(args.warmup)
     torch.cuda.synchronize()
     barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
-        ms_step, ms_bnd, ms_total = lat.step_timed(args.steps)
-    torch.cuda.synchronize()
+        e0.record()
+        lat.step(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
     barrier(world)
+    # the same steps with CUDA events around every kernel (no graphs): the step kernel's
+    # average duration for the roofline and the wall pass's share
+    ms_step, ms_bnd, _ = lat.step_timed(args.steps)
+    torch.cuda.synchronize()
     info = lat.info()
     m_after = lat.mass()
     lat.close()
@@ -729,6 +740,8 @@ def main():
                        "nodes": n_all, "fluid_nodes": n_fluid,
                        "boundary_links": info["n_links"],
                        "l2": "inputs larger than L2 (two 604 MB lattices)",
+                       "stepping": "lbm_step, CUDA graphs of %d steps (kernel times: a second "
+                                   "pass with events around every kernel)" % gs,
                        "parallelism": "replicas" if world > 1 else "single"},
             "mlups_all_nodes": round(world * n_all * args.steps / (ms_total * 1e-3) / 1e6, 1),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
