@@ -77,3 +77,44 @@ def test_status_strings():
     for s in range(7):
         assert lib.lbm_status_string(s).decode()
     assert not math.isnan(1.0)
+
+
+# C structs of the header and their ctypes mirrors in the binding: same size and field offsets
+_STRUCTS = {"lbm_circle": "Circle", "lbm_geometry": "Geometry", "lbm_eos": "Eos",
+            "lbm_options": "Options", "lbm_info_t": "Info", "lbm_domain": "Domain",
+            "lbm_batch_info_t": "BatchInfo", "lbm_tune_trial": "TuneTrial"}
+
+
+def test_header_is_plain_c_and_matches_the_binding_layouts():
+    import os
+    import pathlib
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    tmp_path = pathlib.Path(_build.LIBDIR) / "layout_check"  # in-tree build directory
+    tmp_path.mkdir(parents=True, exist_ok=True)
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "lbm_gb300.h"',
+             "int main(void) {"]
+    for cname, pyname in _STRUCTS.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for field, _ in getattr(lbm, pyname)._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));'
+                         % (cname, field, cname, field))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    # plain C99 with warnings as errors: no C++ or CUDA types in the interface
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                           str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        key, value = line.rsplit(" ", 1)
+        got[key] = int(value)
+    for cname, pyname in _STRUCTS.items():
+        py = getattr(lbm, pyname)
+        assert got["%s size" % cname] == C.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got["%s %s" % (cname, field)] == getattr(py, field).offset, (cname, field)
