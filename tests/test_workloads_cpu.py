@@ -1,0 +1,56 @@
+"""The synthetic workloads follow their stated recipes (sizes, value ranges, seeding) and every
+generated lattice satisfies the library's geometry rule (a cylinder clears the periodic seam)."""
+import math
+
+import numpy as np
+
+from paper_1908_09235_gb300 import workloads
+
+
+def _clears_seam(L, cyl):
+    cx, cy, r = cyl
+    return cx - r - 2 >= 0 and cx + r + 2 <= L - 1 and cy - r - 2 >= 0 and cy + r + 2 <= L - 1
+
+
+def test_fixed_lattices():
+    s, big = workloads.SMALL, workloads.LARGE
+    assert (s.nx, s.ny, s.cyl, s.drop[:3]) == (100, 100, (50.0, 35, 15.0), (50.0, 50.0, 20.0))
+    assert (big.nx, big.ny, big.cyl[2], big.drop[2]) == (4096, 4096, 600.0, 800.0)
+    assert big.drop[:2] == (big.cyl[0], big.cyl[1] + big.cyl[2])  # on the cylinder's top point
+    assert workloads.CS["T_over_Tc"] == 0.86 and s.tau == 1.0 and big.tau == 1.0
+    assert _clears_seam(s.nx, s.cyl) and _clears_seam(big.nx, big.cyl)
+
+
+def test_batched_workload_follows_the_recipe():
+    ws = workloads.batched_domains()
+    assert len(ws) == 512 and ws == workloads.batched_domains()  # seeded: the same every time
+    sides = np.array([w["nx"] for w in ws])
+    assert all(w["nx"] == w["ny"] for w in ws)
+    assert sides.min() >= 64 and sides.max() <= 512 and len(set(sides)) > 200  # uneven
+    for w in ws:
+        L = w["nx"]
+        cx, cy, r = w["cyl"]
+        dcx, dcy, R, _ = w["drop"]
+        assert 0.15 * L <= r <= 0.3 * L and 0.2 * L <= R <= 0.35 * L
+        assert 0.80 <= w["eos"]["T_over_Tc"] <= 0.90 and 0.6 <= w["tau"] <= 1.2
+        assert (dcx, dcy) == (cx, cy + r)
+        assert _clears_seam(L, w["cyl"])
+    # the draws spread over their ranges
+    assert np.ptp([w["tau"] for w in ws]) > 0.5
+
+
+def test_served_stream_follows_the_recipe():
+    rs = workloads.served_requests()
+    assert len(rs) == 2000 and rs == workloads.served_requests()
+    t = np.array([r["arrival"] for r in rs])
+    assert np.all(np.diff(t) > 0)
+    rate = len(t) / t[-1]
+    assert 180 < rate < 220  # Poisson arrivals at 200 per second
+    sides = np.array([r["nx"] for r in rs])
+    assert sides.min() >= 128 and sides.max() <= 1024
+    # log-uniform: the median side near the geometric mean of the range
+    assert abs(math.log(np.median(sides)) - 0.5 * (math.log(128) + math.log(1024))) < 0.1
+    steps = np.array([r["steps"] for r in rs])
+    assert steps.min() >= 2000 and steps.max() <= 20000
+    assert set(r["scheme"] for r in rs) == set(workloads.SERVED_SCHEMES)
+    assert all(_clears_seam(r["nx"], r["cyl"]) for r in rs)
