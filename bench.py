@@ -743,6 +743,23 @@ def main():
                             "kind": "oracle, -fopenmp build of the same source",
                             "sample": "%d FP64 time steps of the %dx%d lattice (%.1f s)"
                                       % (done, w.nx, w.ny, dt)}
+        # the small parity case, 1000 steps: the serial oracle and the GPU (FP64, through lbm_step)
+        from paper_1908_09235_gb300 import workloads
+        sw = workloads.SMALL
+        o_mlups, o_done, o_dt, _ = cpu_oracle_rate(sw, budget_s=15.0, max_steps=1000)
+        slat, _ = make_lattice(sw, lbm.MOD_B, lbm.FP64)
+        slat.step(32)
+        torch.cuda.synchronize()
+        t_s = time.perf_counter()
+        slat.step(1000)
+        slat.mass()  # blocks
+        g_dt = time.perf_counter() - t_s
+        s_fluid = slat.info()["n_fluid"]
+        slat.close()
+        cpu["small_case"] = {"workload": sw.name, "steps": 1000,
+                             "oracle_serial_mlups": round(o_mlups, 3),
+                             "oracle_steps_timed": o_done,
+                             "gpu_fp64_mlups": round(s_fluid * 1000 / g_dt / 1e6, 1)}
 
     if rank == 0:
         line = {
