@@ -132,6 +132,9 @@ def dist_setup():
     if world > 1:
         import torch.distributed as dist
         backend = os.environ.get("LBM_BENCH_BACKEND", "nccl")
+        if backend == "nccl":  # one GPU per rank, chosen before the communicator exists
+            import torch
+            torch.cuda.set_device(local)
         dist.init_process_group(backend)
     return world, rank, local
 
