@@ -10,6 +10,7 @@ import oracle as O
 from paper_1908_09235_gb300 import _build, lbm
 
 HEADER = "include/lbm_gb300.h"
+O_CS = dict(a=0.25, b=4.0, R=1.0, T_over_Tc=0.86, G=-1.0)
 
 
 def _declared():
@@ -118,3 +119,20 @@ def test_header_is_plain_c_and_matches_the_binding_layouts():
         assert got["%s size" % cname] == C.sizeof(py), cname
         for field, _ in py._fields_:
             assert got["%s %s" % (cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_domain_bytes_estimate_is_host_only_and_ordered():
+    # the server's admission estimate (no GPU needed): grows with the lattice, FP64 > FP32 > FP16
+    def dom(L):
+        eos = lbm.make_eos(lbm.EOS_CS, **O_CS)
+        return lbm.make_domain(L, L, 1.0, lbm.MOD_B, circles=[(L / 2, 0.35 * L, 0.15 * L)],
+                               eos=eos, droplet=(L / 2, 0.5 * L, 0.2 * L, 5.0, 0.27, 0.034))
+    sizes = {}
+    for L in (128, 512):
+        for prec in (lbm.FP64, lbm.FP32_DEV, lbm.FP16_DEV):
+            sizes[L, prec] = lbm.lbm_domain_bytes(dom(L), prec)
+    for L in (128, 512):
+        assert sizes[L, lbm.FP64] > sizes[L, lbm.FP32_DEV] > sizes[L, lbm.FP16_DEV]
+        # at least the two lattices of populations
+        assert sizes[L, lbm.FP32_DEV] >= 2 * 36 * L * L
+    assert all(sizes[512, p] > 10 * sizes[128, p] for p in (lbm.FP64, lbm.FP32_DEV))
