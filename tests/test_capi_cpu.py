@@ -136,3 +136,23 @@ def test_domain_bytes_estimate_is_host_only_and_ordered():
         # at least the two lattices of populations
         assert sizes[L, lbm.FP32_DEV] >= 2 * 36 * L * L
     assert all(sizes[512, p] > 10 * sizes[128, p] for p in (lbm.FP64, lbm.FP32_DEV))
+
+
+def test_new_entry_points_reject_invalid_arguments_without_a_gpu():
+    # argument checks come before any CUDA call (documented error behaviour of the header)
+    lib = lbm.load_library()
+    n = C.c_int64()
+    done = C.c_int32()
+    assert lib.lbm_state_bytes(None, C.byref(n)) == 1
+    assert lib.lbm_save_state(None, None, 0) == 1
+    assert lib.lbm_load_state(None, None, 0) == 1
+    for limit in (0, -5, 10**11):  # outside 1 .. 1e10 ns
+        assert lib.lbm_selftest_bounded_wait(limit, 1, None, C.byref(done)) == 1
+    assert lib.lbm_selftest_bounded_wait(1000, 1, None, None) == 1
+    assert lib.lbm_batch_set_schedule(None, 16, lbm.SCHED_CLAIM) == 1
+    assert lib.lbm_batch_tune(None, 3, None) == 1
+    cnt = C.c_int32()
+    assert lib.lbm_batch_tune_trials(None, 0, None, C.byref(cnt)) == 1
+    assert lib.lbm_set_inflow(None, 0.05) == 1
+    fx, fy = C.c_double(), C.c_double()
+    assert lib.lbm_force(None, C.byref(fx), C.byref(fy)) == 1
