@@ -123,13 +123,13 @@ typedef struct {
                         * initial fluid density, set by lbm_init_fields / lbm_init_droplet      */
   int32_t kernel_path; /* step kernel, all with the same results bit for bit:                  *
                         * 0: the fastest measured: for FP32/FP16 deviations with nx % 4 == 0    *
-                        *    and ny >= 8 the vectorised kernel (population vectors of 16 B,     *
-                        *    halo staged by cp.async), otherwise the scalar tile kernel;         *
+                        *    and ny >= 8 (FP16: 12) the vectorised kernel (population vectors   *
+                        *    of 16 B, halo staged by cp.async), otherwise the scalar tiles;      *
                         * 1: the scalar tile kernel (one node per thread and row);              *
                         * 2: FP32 deviations on lattices with nx % 16 == 0, nx, ny >= 64: a     *
                         *    persistent kernel that stages tiles by TMA; otherwise as 0;         *
                         * 3: the vectorised kernel wherever nx % 4 == 0 (FP64: nx % 2 == 0) and *
-                        *    ny >= 8, FP64 included; otherwise the scalar tile kernel            */
+                        *    ny >= 8 (FP16: 12), FP64 included; otherwise the scalar tiles       */
   int32_t track_force; /* nonzero: the wall pass records the momentum exchange for lbm_force   *
                         * (also switched on by lbm_set_inflow); off by default, it costs the   *
                         * wall pass a few microseconds per step; ignored by batches            */

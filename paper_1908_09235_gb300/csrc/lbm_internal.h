@@ -85,7 +85,7 @@ cudaError_t launch_geom_emit(const GeomParams& g, uint8_t* flags, const int2* bl
 
 // step.cu
 // The vectorised step kernel (csrc/step_vec.cu): lattices with nx a multiple of
-// step_vec_width(precision) and ny >= 8.
+// step_vec_width(precision) and ny at least its tile height (8; FP16: 12).
 int step_vec_width(int precision);
 bool step_vec_supported(int precision, int nx, int ny);
 cudaError_t launch_step_vec(int precision, const DevParams& p, const void* fa, void* fb,
