@@ -243,16 +243,82 @@ def test_couette_convergence_order():
     Ns = [32, 64, 128]
     order = {}
     err64 = {}
-    for sch in (O.HBB, O.MLS, O.BOUZIDI_L):
+    for sch in (O.HBB, O.FH, O.MLS, O.BOUZIDI_L):
         e = [_annulus(N, sch) for N in Ns]
         order[sch] = -np.polyfit(np.log(Ns), np.log(e), 1)[0]
         err64[sch] = e[1]
-    # MLS and Bouzidi are second order (Sec. 1); halfway bounce-back on a curved wall is first
-    assert order[O.MLS] > 1.8 and order[O.BOUZIDI_L] > 1.8
+    # the ghost-node schemes (Eqs. (9)-(11)) and Bouzidi are second order on a curved wall
+    # (Sec. 1); halfway bounce-back, a staircase, is first
+    assert order[O.FH] > 1.8 and order[O.MLS] > 1.8 and order[O.BOUZIDI_L] > 1.8
     assert order[O.HBB] < 1.4
-    # the modified schemes are more accurate than halfway bounce-back (Sec. 4.2, Sec. 5)
+    # the modified schemes are more accurate than halfway bounce-back (Sec. 4.2, Sec. 5); they
+    # are first order on a curved wall (Eq. (19) turns a node with one cut link into halfway
+    # bounce-back, and Eq. (18) feeds each node's O(u) imbalance into its rest population)
     for sch in (O.MOD_A, O.MOD_B):
         assert _annulus(64, sch) < err64[O.HBB]
+
+
+# --- Plane Poiseuille flow between flat walls at fraction q (Fig. 3 set-up, driven along x) --
+def _poiseuille_errors(scheme, tau, q_lo, q_hi, Ns=(16, 32, 64), efolds=8.0):
+    """Relative L2 errors of u_x after the flow between flat walls at y = 1 - q_lo and
+    y = ny - 2 + q_hi has settled, for channels of N fluid rows.  A body force g along x gives
+    u(y) = g / (2 nu) (y - y_lo)(y_hi - y); u_max shrinks as 1/N (diffusive scaling)."""
+    errs = []
+    for N in Ns:
+        ny = N + 2
+        y_lo, y_hi = 1 - q_lo, ny - 2 + q_hi
+        nu = (tau - 0.5) / 3
+        g = 8 * nu * (0.64 / N) / (y_hi - y_lo) ** 2
+        s = O.OracleSim(4, ny, tau, scheme=scheme, wall_q_lo=q_lo, wall_q_hi=q_hi, gx=g)
+        y = np.repeat(np.arange(ny, dtype=float)[:, None], 4, axis=1)
+        ue = g / (2 * nu) * (y - y_lo) * (y_hi - y)
+        fl = (s.flags() & 1) == 0
+        s.init_fields(np.ones((ny, 4)), np.where(fl, ue, 0.0), np.zeros((ny, 4)))
+        s.step(int(efolds * (y_hi - y_lo) ** 2 / (math.pi ** 2 * nu)))
+        _, ux, _ = s.fields()
+        errs.append(math.sqrt(np.sum((ux - ue)[fl] ** 2) / np.sum(ue[fl] ** 2)))
+    return errs
+
+
+def _local_orders(errs):
+    return [math.log(errs[k] / errs[k + 1], 2) for k in range(len(errs) - 1)]
+
+
+@pytest.mark.parametrize("scheme,tau", [
+    (O.FH, 0.6), (O.FH, 0.8), (O.MLS, 0.8), (O.BOUZIDI_L, 0.8), (O.BOUZIDI_Q, 0.6),
+    (O.BOUZIDI_Q, 0.8), (O.ZHAO_YONG, 0.8), (O.MOD_A, 0.8), (O.MOD_B, 0.8)])
+def test_poiseuille_second_order(scheme, tau):
+    # Walls at q = 0.3 (bottom) and 0.7 (top) exercise both branches of Eqs. (9)-(13) at once.
+    # Every interpolated scheme places the wall to second order (Sec. 1, Sec. 2.2); halving the
+    # spacing divides the error by 4 (measured local orders 1.98-2.00).  On flat walls each
+    # node's links share q, so the modified schemes coincide with MLS here.
+    orders = _local_orders(_poiseuille_errors(scheme, tau, 0.3, 0.7))
+    assert min(orders) > 1.9, (O.SCHEME_NAMES[scheme], orders)
+
+
+@pytest.mark.parametrize("scheme", [O.MOD_A, O.MOD_B, O.BAO])
+def test_flat_walls_modified_schemes_reduce_to_mls(scheme):
+    # Flow along flat walls with one q per wall: a boundary node's cut links share chi and, in
+    # the layered flow, u_f, and the even part of their ghost equilibria sums to the outgoing
+    # mass, so MLS's per-node imbalance (Eq. (15)) vanishes.  The corrections of Eq. (18),
+    # Eq. (22) and Eq. (23) then change nothing: A, B and Bao are MLS to round-off.  FH, another
+    # q < 1/2 rule (Eq. (9)), is not: the schemes are built on MLS (Sec. 4.1).
+    def run(sch):
+        ny, tau = 34, 0.8
+        s = O.OracleSim(4, ny, tau, scheme=sch, wall_q_lo=0.3, wall_q_hi=0.2, gx=2e-6)
+        y = np.repeat(np.arange(ny, dtype=float)[:, None], 4, axis=1)
+        s.init_fields(np.ones((ny, 4)), 1e-4 * (y - 0.7) * (ny - 1.8 - y), np.zeros((ny, 4)))
+        s.step(20)
+        return s.get_f()
+    f_mls = run(O.MLS)
+    assert np.max(np.abs(run(scheme) - f_mls)) < 1e-14
+    assert np.max(np.abs(run(O.FH) - f_mls)) > 1e-7
+
+
+def test_poiseuille_halfway_bounce_back_first_order():
+    # Halfway bounce-back puts the wall half way along the link whatever q is: first order.
+    orders = _local_orders(_poiseuille_errors(O.HBB, 0.8, 0.3, 0.7))
+    assert all(0.9 < o < 1.1 for o in orders), orders
 
 
 def test_laplace_law():

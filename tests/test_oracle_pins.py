@@ -252,3 +252,27 @@ def test_streaming_translates_planes():
     for a in range(9):
         expect = np.roll(f[a], shift=(3 * EY[a], 3 * EX[a]), axis=(0, 1))
         assert np.max(np.abs(g[a] - expect)) < 1e-12
+
+
+# --- Eqs. (7), (8), (10) and (12) at q = 1, tau = 1 -----------------------------------------
+@pytest.mark.parametrize("scheme", [O.FH, O.MLS, O.MOD_A, O.BOUZIDI_L])
+def test_wall_on_solid_node_gives_symmetric_equilibrium(scheme):
+    # Uniform state f = f_eq(rho, u) next to flat walls through the solid nodes (q = 1), tau = 1,
+    # no force: the collision returns f_eq.  Eq. (10) then has chi = 1 and u_s = 0, so Eq. (7)
+    # returns the ghost equilibrium of Eq. (8) with e.u_s = 0, i.e. the part of f_eq_a that is
+    # even in e_a: (f_eq_a + f_eq_abar) / 2.  Linear Bouzidi at q = 1 (Eq. (12)) averages
+    # f*_a and f*_abar, which is the same mean.  Scheme A keeps MLS's incoming values.
+    rho, ux, uy = 1.1, 0.08, 0.03
+    nx, ny = 4, 6
+    s = O.OracleSim(nx, ny, 1.0, scheme=scheme, wall_q_lo=1.0, wall_q_hi=1.0)
+    s.init_fields(np.full((ny, nx), rho), np.full((ny, nx), ux), np.full((ny, nx), uy))
+    s.step(1)
+    f = s.get_f()
+    feq = O.feq(rho, ux, uy)
+    opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+    for j, into_wall in ((1, (4, 7, 8)), (ny - 2, (2, 5, 6))):
+        for a in into_wall:
+            expect = 0.5 * (feq[a] + feq[opp[a]])
+            assert np.max(np.abs(f[opp[a], j, :] - expect)) < 1e-16, (a, j)
+    # not vacuous: the incoming values differ from halfway bounce-back's f*_a = f_eq_a
+    assert abs(0.5 * (feq[7] + feq[5]) - feq[7]) > 1e-3
