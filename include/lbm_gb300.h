@@ -60,13 +60,15 @@ typedef enum {
   LBM_BOUZIDI_L_A = 9 /* linear Bouzidi, then the rest-population correction of Eq. (18)  */
 } lbm_scheme;
 
-/* How populations are stored in device memory.  Arithmetic is FP64 for LBM_FP64 and FP32 for
- * the deviation formats, which store f_a - w_a rho_ref: LBM_FP32_DEV all nine as FP32;
- * LBM_FP16_DEV the rest population f_0 (which does not stream) as FP32 and the eight moving
- * ones as FP16 (20 bytes per node and lattice).  In both the rest population takes the node's
- * stored mass minus the rounded moving populations, so the bulk step keeps mass to FP32
- * accuracy.  The boundary pass always computes in FP64; with deviation storage its rounding
- * residue is carried per boundary node in FP64 so the mass-conserving schemes stay conserving. */
+/* How populations are stored in device memory.  The per-node step computes in FP64 for
+ * LBM_FP64 and in FP32 for the deviation formats, which store f_a - w_a rho_ref: LBM_FP32_DEV
+ * all nine as FP32; LBM_FP16_DEV the rest population f_0 (which does not stream) as FP32 and the
+ * eight moving ones as FP16 (20 bytes per node and lattice).  In both the rest population takes
+ * the node's stored mass minus the rounded moving populations, so the bulk step keeps mass to
+ * FP32 accuracy.  The boundary pass computes in FP64 for every format (stored values and the
+ * step's moments widened, each incoming value rounded once when stored); with deviation storage
+ * its rounding residue is carried per boundary node in FP64 so the mass-conserving schemes stay
+ * conserving. */
 typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1, LBM_FP16_DEV = 2 } lbm_precision;
 
 typedef enum { LBM_EOS_NONE = 0, LBM_EOS_EXP = 1, LBM_EOS_CS = 2 } lbm_eos_kind;
@@ -120,7 +122,8 @@ typedef struct {
   lbm_free_fn free;
   void* alloc_user;
   double rho_ref;      /* reference density of the deviation formats; <= 0: the smallest       *
-                        * initial fluid density, set by lbm_init_fields / lbm_init_droplet      */
+                        * initial fluid density, set by lbm_init_fields / lbm_init_droplet.     *
+                        * Used rounded to the nearest FP32 value                                */
   int32_t kernel_path; /* step kernel, all with the same results bit for bit:                  *
                         * 0: the fastest measured: for FP32/FP16 deviations with nx % 4 == 0    *
                         *    and ny >= 8 (FP16: 12) the vectorised kernel (population vectors   *
@@ -252,6 +255,16 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* buf, int64_t bytes);
 lbm_status lbm_selftest_bounded_wait(int64_t limit_ns, int32_t complete, void* stream,
                                      int32_t* completed);
 
+/* Throughput of the GPU's FP64 fused multiply-add pipe, measured (measurement support; the
+ * paper has no counterpart: the FP64 step of the method is bound by this pipe on GB300, and its
+ * roofline needs the pipe's rate).  One untimed and one timed launch of a kernel that fills the
+ * GPU with one wave of resident blocks, each thread running 8 independent chains of iters
+ * dependent FP64 FMAs; CUDA events on `stream` (cudaStream_t or NULL) around the timed launch.
+ *   iters    FMAs per chain, 1 .. 2^24 (about 1e5 gives a launch of tens of milliseconds)
+ *   gflops   receives 2 x FMAs / time in GFLOP/s      ms  receives the timed launch in ms
+ * Blocks until done.  LBM_EINVAL for bad arguments, LBM_ECUDA if a CUDA call fails. */
+lbm_status lbm_probe_fp64_fma(int32_t iters, void* stream, double* gflops, double* ms);
+
 /* Total mass of caller-owned device arrays without allocating any memory.  (This entry point
  * has no counterpart in the paper; it serves callers that cannot allocate device memory: a host
  * framework that already holds the device memory in its own pool, or a latency-critical loop
@@ -269,7 +282,9 @@ lbm_status lbm_selftest_bounded_wait(int64_t limit_ns, int32_t complete, void* s
  * 8192 x 8192 = 67,108,864 nodes (larger lattices return LBM_EINVAL).  All calls on a device share
  * that array: calls whose kernels overlap on the GPU race and give wrong results, so serialise
  * them (e.g. one stream).  The first call on a device looks up the array's device address (no
- * allocation) and should come before any stream capture.  Returns LBM_EINVAL for bad arguments,
+ * allocation) and should come before any stream capture; the address is kept for the life of
+ * the process, so resetting the device (cudaDeviceReset) after that first call is not supported:
+ * the next call would launch with the old address.  Returns LBM_EINVAL for bad arguments,
  * LBM_ECUDA if a launch fails; the mass and status arrive on the stream. */
 lbm_status lbm_mass_noalloc(const void* f, const uint8_t* flags, int32_t nx, int32_t ny,
                             int32_t precision, double rho_ref, double* mass_out,

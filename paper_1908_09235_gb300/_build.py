@@ -18,7 +18,7 @@ LIB = os.path.join(LIBDIR, "liblbm_gb300.so")
 CHECKED_LIB = os.path.join(LIBDIR, "liblbm_gb300_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["step.cu", "step_vec.cu", "step_tma.cu", "boundary.cu", "geometry.cu", "ledger.cu", "capi.cu",
-                "batch.cu", "mass_noalloc.cu"]
+                "batch.cu", "mass_noalloc.cu", "probe.cu"]
 CXX_SOURCES = ["eos_host.cpp"]
 
 

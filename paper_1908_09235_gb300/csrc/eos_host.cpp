@@ -157,6 +157,9 @@ static void fill(Consts<C>& k, const DevParams& p) {
 }
 
 void finalize_consts(DevParams& p) {
+  // The deviation formats store f_a - w_a rho_ref; the FP32 step kernels hold rho_ref as a
+  // float, the wall pass and the ledger as a double: one value, representable in both.
+  p.rho_ref = (double)(float)p.rho_ref;
   fill(p.cd, p);
   fill(p.cf, p);
 }

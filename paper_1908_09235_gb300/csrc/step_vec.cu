@@ -239,7 +239,8 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
 
   // ---- staged copies: ring rows (slot s at x0 + V (s - 1), s = 0 .. nv + 1) and the side
   // vectors (x0 - V, x0 + V nv) of the own rows.  Warp w copies the ring's (row, plane) pairs
-  // w, w + 8, w + 16, one slot per lane, and the side vectors of its own row. ----
+  // w, w + VH, w + 2 VH (those below 18), one slot per lane, and the side vectors of its own
+  // row. ----
   // nodes whose psi comes from the staged populations: the ring rows' x0 - 1 .. x0 + V nv
   // (rj each, at most RJ), then x0 - 1 and x0 + V nv of each own row
   constexpr int RJ = TW + 2;
@@ -537,7 +538,9 @@ cudaError_t launch_vec_s(const DevParams& p, const void* fa, void* fb, const uin
 int step_vec_width(int precision) { return precision == LBM_FP64 ? 2 : 4; }
 
 bool step_vec_supported(int precision, int nx, int ny) {
-  const int vh = precision == LBM_FP16_DEV ? Vec<__half>::VH : Vec<float>::VH;
+  const int vh = precision == LBM_FP16_DEV   ? Vec<__half>::VH
+                 : precision == LBM_FP32_DEV ? Vec<float>::VH
+                                             : Vec<double>::VH;
   return nx % step_vec_width(precision) == 0 && ny >= vh;
 }
 

@@ -34,7 +34,8 @@ EXPORTS = ("lbm_create", "lbm_coexistence", "lbm_init_fields", "lbm_init_droplet
            "lbm_batch_domain", "lbm_batch_tune", "lbm_batch_info", "lbm_domain_bytes",
            "lbm_batch_last_error", "lbm_batch_destroy", "lbm_batch_poll", "lbm_set_inflow",
            "lbm_force", "lbm_batch_tune_trials", "lbm_batch_set_schedule", "lbm_state_bytes",
-           "lbm_save_state", "lbm_load_state", "lbm_selftest_bounded_wait")
+           "lbm_save_state", "lbm_load_state", "lbm_selftest_bounded_wait",
+           "lbm_probe_fp64_fma")
 
 # lbm_schedule: how the CTAs of a batch's step kernel take tiles from its queue
 SCHED_STRIDED, SCHED_CLAIM, SCHED_CLAIM_LARGEST_FIRST = 0, 1, 2
@@ -167,6 +168,7 @@ def load_library(build_if_missing=True):
             "lbm_load_state": (C.c_int, [P, C.c_void_p, C.c_int64]),
             "lbm_selftest_bounded_wait": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p,
                                                     C.POINTER(C.c_int32)]),
+            "lbm_probe_fp64_fma": (C.c_int, [C.c_int32, C.c_void_p, D, D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -290,6 +292,20 @@ def lbm_selftest_bounded_wait(limit_ns, complete, stream=None):
     st = load_library().lbm_selftest_bounded_wait(int(limit_ns), int(complete),
                                                   C.c_void_p(int(stream)), C.byref(done))
     return st, done.value
+
+
+def lbm_probe_fp64_fma(iters=100000, stream=None):
+    """(GFLOP/s, ms) of the FP64 FMA pipe, measured on the current device; see
+    include/lbm_gb300.h."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    gf, ms = C.c_double(), C.c_double()
+    st = load_library().lbm_probe_fp64_fma(int(iters), C.c_void_p(int(stream)), C.byref(gf),
+                                           C.byref(ms))
+    if st != 0:
+        raise LBMError(st, "lbm_probe_fp64_fma")
+    return gf.value, ms.value
 
 
 def lbm_info(ctx):

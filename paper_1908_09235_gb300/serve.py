@@ -73,6 +73,7 @@ class Server:
         self.batch = lbm.Batch(precision, lbm.EOS_CS, max_domains=max_slots)
         self.max_concurrent = 0
         self.peak_bytes = 0
+        self.slot_rid = {}  # slot -> rid of the request it holds (for collect functions)
 
     def close(self):
         self.batch.close()
@@ -80,7 +81,9 @@ class Server:
     def run(self, requests, collect=summary_result, realtime=True):
         """Serve `requests` (dicts with at least rid, arrival, nx, ny, steps, ...).  With realtime
         the arrivals follow the wall clock from the start of the call; otherwise every request
-        is available at once.  Returns the list of Served records in completion order."""
+        is available at once.  collect(batch, slot) makes a finished request's result while it
+        is still in the batch (self.slot_rid[slot] names the request).  Returns the list of
+        Served records in completion order."""
         b = self.batch
         pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
         active = {}
@@ -100,6 +103,7 @@ class Server:
                                            % (req["rid"], need, self.hbm_bytes))
                     break
                 slot = b.add(dom, req["steps"])
+                self.slot_rid[slot] = req["rid"]
                 rec = Served(rid=req["rid"], arrival=req["arrival"] if realtime else 0.0,
                              nodes=req["nx"] * req["ny"], steps=req["steps"], slot=slot,
                              bytes=need, admitted=self.clock() - t0)
@@ -124,6 +128,54 @@ class Server:
                     del active[slot]
                     done.append(rec)
         return done
+
+
+def request_lattice(req, precision=lbm.FP64):
+    """A standalone lattice (lbm_create) of a request dict, initialised with its droplet."""
+    eos = lbm.make_eos(lbm.EOS_CS, **req["eos"])
+    rl, rv = lbm.lbm_coexistence(eos)
+    eos.rho_wall = rv
+    lat = lbm.Lattice(req["nx"], req["ny"], req["tau"], lbm.SCHEMES[req["scheme"]]
+                      if isinstance(req["scheme"], str) else req["scheme"], circles=[req["cyl"]],
+                      eos=eos, precision=precision)
+    lat.init_droplet(*req["drop"], rl, rv)
+    return lat
+
+
+def lattice_result(lat):
+    """Result of a finished standalone run, as summary_result makes it for a batch member."""
+    try:
+        m = lat.mass()
+    except lbm.LBMError:
+        return {"mass": float("nan"), "unstable": True}
+    rho, _, _ = lat.fields()
+    return {"mass": m, "rho_min": float(np.nanmin(rho)), "rho_max": float(np.nanmax(rho)),
+            "unstable": False}
+
+
+def run_one_at_a_time(requests, precision=lbm.FP64, make=request_lattice,
+                      collect=lattice_result, clock=time.perf_counter, sleep=time.sleep):
+    """The plain serving loop the continuous-batching server is compared with: requests in
+    arrival order, one lattice at a time (created, stepped to its budget, its result read back,
+    destroyed), the next one started when the previous is done and it has arrived.  Arrivals
+    follow the clock from the start of the call; latency is arrival to result on the host.
+    Returns Served records in completion order."""
+    done = []
+    t0 = clock()
+    for req in sorted(requests, key=lambda r: r["arrival"]):
+        wait = req["arrival"] - (clock() - t0)
+        if wait > 0:
+            sleep(wait)
+        rec = Served(rid=req["rid"], arrival=req["arrival"], nodes=req["nx"] * req["ny"],
+                     steps=req["steps"], admitted=clock() - t0)
+        lat = make(req, precision)
+        lat.step(req["steps"])
+        rec.result = collect(lat) if collect else {}
+        rec.fluid_nodes = lat.info()["n_fluid"]
+        rec.finished = clock() - t0
+        lat.close()
+        done.append(rec)
+    return done
 
 
 def latency_stats(done):

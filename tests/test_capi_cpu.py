@@ -17,7 +17,7 @@ def _declared():
     import os
     src = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), HEADER)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_builds_and_exports_every_declared_symbol():
@@ -149,6 +149,10 @@ def test_new_entry_points_reject_invalid_arguments_without_a_gpu():
     for limit in (0, -5, 10**11):  # outside 1 .. 1e10 ns
         assert lib.lbm_selftest_bounded_wait(limit, 1, None, C.byref(done)) == 1
     assert lib.lbm_selftest_bounded_wait(1000, 1, None, None) == 1
+    gf, ms = C.c_double(), C.c_double()
+    for iters in (0, -1, 2**24 + 1):
+        assert lib.lbm_probe_fp64_fma(iters, None, C.byref(gf), C.byref(ms)) == 1
+    assert lib.lbm_probe_fp64_fma(1000, None, None, C.byref(ms)) == 1
     assert lib.lbm_batch_set_schedule(None, 16, lbm.SCHED_CLAIM) == 1
     assert lib.lbm_batch_tune(None, 3, None) == 1
     cnt = C.c_int32()

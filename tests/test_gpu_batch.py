@@ -184,3 +184,23 @@ def test_full_batched_workload_sampled_members(gpu_lib):
         fields, _ = _alone(ws[k], lbm.MOD_B, lbm.FP32_DEV, 40)
         _same(b.fields(slots[k]), fields)
     b.close()
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_DEV])
+def test_batch_flags_the_lattices_the_oracle_flags(gpu_lib, precision):
+    # the smallest members of the 512-lattice workload: the batch reports LBM_EUNSTABLE for
+    # exactly the lattices whose FP64 oracle run diverges within the same steps
+    from test_workloads_cpu import oracle_diverges
+    ws = [w for w in workloads.batched_domains() if w["nx"] <= 70]
+    b = lbm.Batch(precision, lbm.EOS_CS, max_domains=len(ws))
+    slots = [b.add(_member(w, lbm.MOD_B, precision), 300) for w in ws]
+    b.step(300)
+    for w, s in zip(ws, slots):
+        try:
+            b.mass(s)
+            gpu_unstable = False
+        except lbm.LBMError as e:
+            assert e.status == 4  # LBM_EUNSTABLE
+            gpu_unstable = True
+        assert gpu_unstable == oracle_diverges(w, 300), w["name"]
+    b.close()

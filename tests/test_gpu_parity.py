@@ -253,8 +253,10 @@ def test_droplet_on_cylinder_fp32_dev(gpu_lib, scheme):
 
 # ---- vectorised step kernel gives the same bits as the scalar tile kernel ----------------------
 # (256, 192): whole tiles; (100, 100): one ragged tile column (25 of 32 FP32 lanes) and a ragged
-# tile row; (132, 68): a last tile one vector wide; (16, 12): one tile that wraps onto itself.
-VEC_SHAPES = [(256, 192), (100, 100), (132, 68), (16, 12)]
+# tile row; (132, 68): a last tile one vector wide; (16, 12): one tile that wraps onto itself;
+# (64, 10): ny between the FP32/FP64 tile height (8) and the FP16 one (12), where FP16 takes the
+# scalar tiles and the other formats the vectorised kernel.
+VEC_SHAPES = [(256, 192), (100, 100), (132, 68), (16, 12), (64, 10)]
 
 
 def _two_phase(nx, ny, precision, path, steps, scheme=lbm.MOD_B):

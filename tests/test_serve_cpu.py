@@ -93,3 +93,36 @@ def test_fifo_model_and_latency_statistics():
     st = serve.latency_stats([R(float(x)) for x in range(1, 101)])
     assert st["p50_s"] == pytest.approx(50.5) and st["max_s"] == 100.0
     assert st["p99_s"] == pytest.approx(99.01)
+
+
+def test_one_at_a_time_loop_follows_arrivals_and_matches_the_fifo_model():
+    # The plain FP64 loop, run with a fake lattice whose step costs steps / 100 seconds of a
+    # fake clock: requests run in arrival order, each waits for its arrival and for the one
+    # before it, and the latencies equal the FIFO model's for the same service times.
+    clock = {"t": 0.0}
+
+    class FakeLattice:
+        def __init__(self, req, precision):
+            self.req = req
+            assert precision == lbm.FP64
+
+        def step(self, n):
+            clock["t"] += n / 100.0
+
+        def info(self):
+            return {"n_fluid": 7}
+
+        def close(self):
+            pass
+
+    rs = _requests(4, steps=200)
+    for r, a in zip(rs, (0.0, 0.5, 1.0, 9.0)):
+        r["arrival"] = a
+    done = serve.run_one_at_a_time(rs, make=FakeLattice, collect=None,
+                                   clock=lambda: clock["t"],
+                                   sleep=lambda s: clock.__setitem__("t", clock["t"] + s))
+    assert [r.rid for r in done] == [r["rid"] for r in rs]
+    expect = serve.fifo_latencies([r["arrival"] for r in rs], [2.0] * 4)
+    assert np.allclose([r.latency for r in done], expect)
+    assert np.allclose([r.latency for r in done], [2.0, 3.5, 5.0, 2.0])
+    assert all(r.fluid_nodes == 7 for r in done)
