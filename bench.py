@@ -27,6 +27,12 @@ UNIT = "MLUPS"
 SCHEME_NAMES = ("mls", "bouzidi_l", "zhao_yong", "mod_a", "mod_b")
 
 
+# FP64 pipe operations (DFMA + DADD + DMUL thread instructions) per fluid-node update of the FP64
+# step kernel, counted by ncu on the 2048^2 case (profiles/step_kernel_fp64_4096.md): with the
+# measured FMA rate of the pipe it gives the FP64 step's ALU roofline
+FP64_PIPE_OPS_PER_NODE = 128
+
+
 def bytes_per_update(precision):
     # algorithmic traffic of one fluid-node update: 9 populations read + 9 written
     # (fp16_dev: the rest population in FP32, the eight moving ones in FP16)
@@ -384,30 +390,109 @@ def run_cylinder_flow(args):
                       "runs": runs}), flush=True)
 
 
-def run_precision_report(args):
-    """The reduced-precision formats on long runs: FP32 and FP16 deviation storage (FP32
-    arithmetic, FP64 per-node mass bookkeeping in the wall pass, FP64 ledger) on droplet-on-
-    cylinder lattices of the given sides (the 4096^2 geometry scaled: cylinder 600/4096 L,
-    droplet 800/4096 L), scheme B.  Total-mass drift |m/m0 - 1| every --report-every steps; at
-    sides <= 2048 also the rho and u errors after the last step against the FP64 path on the same
-    lattice (the FP64 path is the oracle's stand-in here: the parity tests hold it to 1e-11 of
-    the CPU oracle, which would need hours for 20000 steps of 2048^2 on one core)."""
+def _field_errors(got, ref):
     import numpy as np
+    m = np.isfinite(ref[0])
+    if not np.array_equal(np.isfinite(got[0]), m) and not np.all(np.isfinite(got[0][m])):
+        return {"finite": False}
+    drho = np.abs(got[0][m] - ref[0][m])
+    du = np.maximum(np.abs(got[1][m] - ref[1][m]), np.abs(got[2][m] - ref[2][m]))
+    return {"finite": True,
+            "rho_normwise": float("%.3e" % (drho.max() / np.max(ref[0][m]))),
+            "rho_max_rel": float("%.3e" % np.max(drho / ref[0][m])),
+            "rho_rms": float("%.3e" % np.sqrt(np.mean(drho ** 2))),
+            "u_max_abs": float("%.3e" % du.max()),
+            "u_max_ref": float("%.3e" % np.max(np.hypot(ref[1][m], ref[2][m])))}
+
+
+def precision_measure(side, checkpoints, fp16_bound=1e-3):
+    """The storage formats against the FP64 CPU oracle on one droplet-on-cylinder lattice of
+    the given side (the 4096^2 geometry scaled: cylinder 600/4096 L, droplet 800/4096 L), scheme
+    B: FP64, FP32 deviation and FP16 deviation storage on the GPU and the oracle's -fopenmp build
+    on all host cores, compared after each step count in `checkpoints` (rho and u errors,
+    total-mass drift).  Also the last checkpoint up to which the FP16 format's normwise rho
+    error stays below fp16_bound."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_1908_09235_gb300 import lbm, workloads
+    w = workloads.droplet_on_cylinder(side, 600.0 / 4096 * side, 800.0 / 4096 * side)
+    openmp = True
+    try:
+        O.build_oracle(openmp=True)
+    except Exception:  # no OpenMP runtime on this host: the serial build
+        openmp = False
+    c = w.eos
+    Tc, _ = O.cs_critical(c["a"], c["b"], c["R"])
+    rl, rv = O.cs_coexistence(c["a"], c["b"], c["R"], c["T_over_Tc"] * Tc)
+    s = O.OracleSim(w.nx, w.ny, w.tau, scheme=O.MOD_B, circles=w.circles, eos=O.EOS_CS, G=c["G"],
+                    a=c["a"], b=c["b"], R=c["R"], T_over_Tc=c["T_over_Tc"], rho_wall=rv,
+                    openmp=openmp)
+    s.init_droplet(*w.drop, rl, rv)
+    lats, m0 = {}, {}
+    for pname in ("fp64", "fp32_dev", "fp16_dev"):
+        lats[pname], _ = make_lattice(w, lbm.MOD_B, lbm.PRECISIONS[pname])
+        m0[pname] = lats[pname].mass()
+    rows, done, oracle_s = [], 0, 0.0
+    fp16_ok_until = 0
+    checkpoints = sorted(int(c) for c in checkpoints)
+    steps = checkpoints[-1]
+    for target in checkpoints:
+        n = target - done
+        t0 = time.perf_counter()
+        s.step(n)
+        oracle_s += time.perf_counter() - t0
+        ref = s.fields()
+        done += n
+        row = {"step": done}
+        for pname, lat in lats.items():
+            lat.step(n)
+            try:
+                drift = abs(lat.mass() / m0[pname] - 1.0)
+            except lbm.LBMError:
+                drift = None
+            e = _field_errors(lat.fields(), ref)
+            e["mass_drift"] = float("%.3e" % drift) if drift is not None else None
+            row[pname] = e
+        if row["fp16_dev"].get("finite") and row["fp16_dev"]["rho_normwise"] < fp16_bound and \
+                fp16_ok_until == done - n:
+            fp16_ok_until = done  # every earlier checkpoint was within the bound too
+        rows.append(row)
+    for lat in lats.values():
+        lat.close()
+    torch.cuda.synchronize()
+    n_fluid = int((s.flags() & 1 == 0).sum())
+    return {"workload": w.name, "scheme": "mod_b", "steps": steps, "checkpoints_steps": checkpoints,
+            "oracle": {"build": "-fopenmp" if openmp else "serial",
+                       "threads": O.num_threads(openmp), "seconds": round(oracle_s, 1),
+                       "mlups": round(n_fluid * steps / oracle_s / 1e6, 2)},
+            "fp16_normwise_bound": fp16_bound,
+            "fp16_within_bound_through_step": fp16_ok_until,
+            "checkpoints": rows}
+
+
+def run_precision_report(args):
+    """The reduced-precision formats on long runs (--precision-report): against the FP64 CPU
+    oracle on the smallest side of --report-sides (every --report-every steps), and total-mass
+    drift of the FP32 and FP16 formats on the larger sides (no oracle there: its run would take
+    hours)."""
     import torch
 
     from paper_1908_09235_gb300 import lbm, workloads
     torch.cuda.set_device(0)
+    sides = sorted(int(v) for v in args.report_sides.split(","))
     steps, every = args.report_steps, args.report_every
-    runs = []
-    for L in (int(v) for v in args.report_sides.split(",")):
+    marks = sorted({c for c in (10, 20, 50, 100, 200, 500, 1000, 2000, 5000, 10000) if c < steps}
+                   | set(range(every, steps + 1, every)) | {steps})
+    out = {"report": "reduced precision, droplet on cylinder, scheme B", "steps": steps,
+           "vs_oracle": precision_measure(sides[0], marks), "drift_only": []}
+    for L in sides[1:]:
         w = workloads.droplet_on_cylinder(L, 600.0 / 4096 * L, 800.0 / 4096 * L)
-        ref = None
-        for pname in (("fp64",) if L <= 2048 else ()) + ("fp32_dev", "fp16_dev"):
+        for pname in ("fp32_dev", "fp16_dev"):
             lat, _ = make_lattice(w, lbm.MOD_B, lbm.PRECISIONS[pname])
             m0 = lat.mass()
             drift, done, status = [], 0, "ok"
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
             while done < steps:
                 n = min(every, steps - done)
                 lat.step(n)
@@ -415,33 +500,16 @@ def run_precision_report(args):
                 try:
                     drift.append(abs(lat.mass() / m0 - 1.0))
                 except lbm.LBMError as e:
-                    status = e.args[-1] if e.args else "unstable"
+                    status = str(e)
                     break
-            wall = time.perf_counter() - t0
-            n_fluid = lat.info()["n_fluid"]
-            run = {"side": L, "storage": pname, "steps": done, "status": status,
-                   "mlups_incl_mass_reads": round(n_fluid * done / wall / 1e6, 1),
-                   "mass_drift_every_%d" % every: [float("%.3e" % d) for d in drift],
-                   "max_mass_drift": float("%.3e" % max(drift)) if drift else None}
-            if L <= 2048 and status == "ok":
-                rho, ux, uy = lat.fields()
-                if pname == "fp64":
-                    ref = (rho, ux, uy)
-                elif ref is not None:
-                    m = np.isfinite(ref[0])
-                    drho = np.abs(rho[m] - ref[0][m])
-                    du = np.maximum(np.abs(ux[m] - ref[1][m]), np.abs(uy[m] - ref[2][m]))
-                    umax = float(np.max(np.hypot(ref[1][m], ref[2][m])))
-                    run["vs_fp64"] = {
-                        "rho_max_abs": float("%.3e" % drho.max()),
-                        "rho_normwise": float("%.3e" % (drho.max() / np.max(ref[0][m]))),
-                        "rho_rms": float("%.3e" % np.sqrt(np.mean(drho ** 2))),
-                        "u_max_abs": float("%.3e" % du.max()),
-                        "u_max_ref": float("%.3e" % umax)}
             lat.close()
-            runs.append(run)
-    print(json.dumps({"report": "reduced precision, droplet on cylinder, scheme B",
-                      "steps": steps, "runs": runs}), flush=True)
+            out["drift_only"].append({"side": L, "storage": pname, "steps": done,
+                                      "status": status,
+                                      "mass_drift_every_%d" % every:
+                                          [float("%.3e" % d) for d in drift],
+                                      "max_mass_drift": float("%.3e" % max(drift))
+                                      if drift else None})
+    print(json.dumps(out), flush=True)
 
 
 def run_profile_case(args):
@@ -479,25 +547,25 @@ def _batch_member(lbm, w):
                            droplet=tuple(w["drop"]) + (rl, rv))
 
 
-def run_batched(args):
-    """512 uneven droplet-on-cylinder lattices (sides 64..512, seeded) in one batch: one set of
-    launches per time step under a CUDA graph, tile height and tile-queue schedule chosen by the
-    batch's tuner.
-    Compared with the plain loop that advances one FP64 lattice at a time."""
+def batched_measure(n_domains, precision, steps, warmup, base_count=16):
+    """The batched workload (n_domains uneven droplet-on-cylinder lattices, sides 64..512,
+    seeded) in one batch: one set of launches per time step under a CUDA graph, tile height and
+    tile-queue schedule chosen by the batch's tuner; `steps` timed steps of every lattice.
+    Throughput over all lattices and over the lattices that stayed finite (a diverged lattice
+    costs the same per step but its result is void), beside the plain loop that advances one
+    FP64 lattice at a time (the first base_count lattices, 10 steps each)."""
     import torch
 
     from paper_1908_09235_gb300 import lbm, workloads
-    torch.cuda.set_device(0)
-    ws = workloads.batched_domains(args.batch_domains)
-    prec = lbm.PRECISIONS[args.precision]
+    ws = workloads.batched_domains(n_domains)
+    prec = lbm.PRECISIONS[precision]
     b = lbm.Batch(prec, lbm.EOS_CS, max_domains=len(ws))
     slots = [b.add(_batch_member(lbm, w), 10**9) for w in ws]
-    rows = b.tune(3)
+    b.tune(3)
     trials = b.tune_trials()
     info = b.info()
-    b.step(args.warmup)
+    b.step(warmup)
     torch.cuda.synchronize()
-    steps = args.batch_steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(0) as clk:
         e0.record()
@@ -506,17 +574,17 @@ def run_batched(args):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     split = b.step_timed(5)
-    unstable = 0
-    for s_ in slots:
+    unstable, finite_nodes = [], 0
+    for w, s_ in zip(ws, slots):
         try:
             b.mass(s_)
+            finite_nodes += lbm.lbm_info(b.ctx(s_))["n_fluid"]
         except lbm.LBMError:
-            unstable += 1
+            unstable.append(w["name"])
     b.close()
     value = info["fluid_nodes"] * steps / (ms * 1e-3) / 1e6
-    # baseline: plain loop, one FP64 lattice at a time (first 16 lattices, 10 steps each)
     base_nodes, base_ms = 0, 0.0
-    for w in ws[:16]:
+    for w in ws[:base_count]:
         eos = lbm.make_eos(lbm.EOS_CS, **w["eos"])
         rl, rv = lbm.lbm_coexistence(eos)
         eos.rho_wall = rv
@@ -528,67 +596,86 @@ def run_batched(args):
         base_ms += t
         lat.close()
     base = base_nodes / (base_ms * 1e-3) / 1e6
-    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1,
-            "steps": steps, "warmup": args.warmup,
-            "ms_per_step": round(ms / steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if prec != lbm.FP64 else "f64", "data": "synthetic",
-            "config": {"workload": "batched_droplets_%d" % len(ws), "storage": args.precision,
-                       "scheme": "mod_b", "lattices": info["active"], "nodes": info["nodes"],
-                       "fluid_nodes": info["fluid_nodes"], "tiles": info["tiles"],
-                       "tile": [info["tile_cols"], info["tile_rows"]],
-                       "schedule": SCHED_NAMES[info["schedule"]], "graph": True},
+    return {"workload": "batched_droplets_%d" % len(ws), "storage": precision, "scheme": "mod_b",
+            "steps": steps, "lattices": info["active"], "nodes": info["nodes"],
+            "fluid_nodes": info["fluid_nodes"], "tiles": info["tiles"],
+            "tile": [info["tile_cols"], info["tile_rows"]],
+            "schedule": SCHED_NAMES[info["schedule"]], "graph": True,
+            "ms_per_step": round(ms / steps, 4), "mlups": round(value, 1),
+            "mlups_finite_lattices": round(finite_nodes * steps / (ms * 1e-3) / 1e6, 1),
+            "unstable_lattices": len(unstable), "unstable_names": unstable,
             "tuner_ms_per_launch": {"%dx%d/%s" % (info["tile_cols"], r, SCHED_NAMES[sc]):
-                                    round(ms, 4) for r, sc, ms in trials},
+                                    round(t, 4) for r, sc, t in trials},
             "split_ms_per_step": {"step_kernel": round(split[1] / 5, 4),
                                   "boundary_and_advance": round(split[2] / 5, 4)},
-            "unstable_lattices": unstable,
             "plain_fp64_loop_mlups": round(base, 1),
             "speedup_vs_plain_fp64_loop": round(value / base, 2),
             "clocks": clk.summary()}
+
+
+def run_batched(args):
+    """The batched workload as its own JSON line (--batched)."""
+    import torch
+    torch.cuda.set_device(0)
+    r = batched_measure(args.batch_domains, args.precision, args.batch_steps, args.warmup)
+    line = {"metric": METRIC, "value": r["mlups"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.batch_steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {k: r[k] for k in ("workload", "storage", "scheme", "lattices", "nodes",
+                                         "fluid_nodes", "tiles", "tile", "schedule", "graph")},
+            "batched": r, "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
-    """Served stream of droplet-on-cylinder requests (Poisson arrivals, side log-uniform,
-    steps uniform, scheme from the five variants) through the continuous-batching server with
-    FP32 deviation storage; compared with the plain loop that runs one FP64 lattice at a time."""
+def served_measure(n, rate, steps_lo, steps_hi, slots, hbm_gb, chunk, accuracy_sample=0,
+                   plain_subset=0):
+    """A served stream of droplet-on-cylinder requests (Poisson arrivals, side log-uniform
+    128..1024, steps uniform, scheme from the five variants) through the continuous-batching
+    server with FP32 deviation storage.  Beside it:
+    - the plain loop that runs one FP64 lattice at a time: modelled for the whole stream (FIFO
+      queue with measured FP64 rates per size) and, for the first plain_subset arrivals, run
+      for real (serve.run_one_at_a_time) next to the model's figures for the same subset;
+    - accuracy: up to accuracy_sample finished stable requests (side <= 512) re-run alone in
+      FP64; the served FP32 density against it."""
     import numpy as np
     import torch
 
     from paper_1908_09235_gb300 import lbm, serve, workloads
-    torch.cuda.set_device(0)
-    reqs = workloads.served_requests(n=args.serve_requests, rate=args.serve_rate,
-                                     steps_lo=args.serve_steps_lo, steps_hi=args.serve_steps_hi)
-    srv = serve.Server(precision=lbm.FP32_DEV, max_slots=args.serve_slots,
-                       hbm_bytes=int(args.serve_hbm_gb * 2**30) if args.serve_hbm_gb else None,
-                       chunk=args.serve_chunk)
+    reqs = workloads.served_requests(n=n, rate=rate, steps_lo=steps_lo, steps_hi=steps_hi)
+    srv = serve.Server(precision=lbm.FP32_DEV, max_slots=slots,
+                       hbm_bytes=int(hbm_gb * 2**30) if hbm_gb else None, chunk=chunk)
+    want = [r["rid"] for r in reqs if r["nx"] <= 512][:3 * accuracy_sample]
+    kept = {}
+
+    def collect(b, slot):
+        res = serve.summary_result(b, slot)
+        rid = srv.slot_rid[slot]
+        if rid in want and not res["unstable"] and len(kept) < accuracy_sample:
+            kept[rid] = b.fields(slot)[0]
+        return res
+
     t0 = time.perf_counter()
     with Clocks(0) as clk:
-        done = srv.run(reqs)
+        done = srv.run(reqs, collect=collect)
     makespan = time.perf_counter() - t0
     srv.close()
     work = sum(r.fluid_nodes * r.steps for r in done)
-    value = work / makespan / 1e6
+    stable_work = sum(r.fluid_nodes * r.steps for r in done if not r.result.get("unstable"))
     stats = serve.latency_stats(done)
     unstable = sum(1 for r in done if r.result.get("unstable"))
-    # plain loop: one FP64 lattice at a time; per-size FP64 step rate and set-up time measured
-    # here, latencies from a FIFO queue on the same arrivals (a model, not a replay)
+    # the plain loop: per-size FP64 step rate and set-up time measured here
     sizes = [128, 256, 512, 1024]
-    rate, setup = {}, {}
+    rate_by, setup = {}, {}
     for L in sizes:
         req = dict(workloads.served_requests(n=1, side_lo=L, side_hi=L)[0])
         t1 = time.perf_counter()
-        eos = lbm.make_eos(lbm.EOS_CS, **req["eos"])
-        rl, rv = lbm.lbm_coexistence(eos)
-        eos.rho_wall = rv
-        lat = lbm.Lattice(L, L, req["tau"], lbm.MOD_B, circles=[req["cyl"]], eos=eos)
-        lat.init_droplet(*req["drop"], rl, rv)
+        lat = serve.request_lattice(req)
         lat.mass()
         setup[L] = time.perf_counter() - t1
         lat.step_timed(3)
         _, _, ms = lat.step_timed(20)
-        rate[L] = lat.info()["n_fluid"] * 20 / (ms * 1e-3)
+        rate_by[L] = lat.info()["n_fluid"] * 20 / (ms * 1e-3)
         lat.fields()
         lat.close()
     logs = np.log(sizes)
@@ -596,33 +683,87 @@ def run_serve(args):
     def interp(d, L):
         return float(np.exp(np.interp(np.log(L), logs, np.log([d[s] for s in sizes]))))
     by_id = {r["rid"]: r for r in reqs}
+    order = sorted(done, key=lambda r: r.arrival)
     service = [interp(setup, by_id[r.rid]["nx"]) + r.fluid_nodes * r.steps /
-               interp(rate, by_id[r.rid]["nx"]) for r in sorted(done, key=lambda r: r.arrival)]
-    arrivals = [r.arrival for r in sorted(done, key=lambda r: r.arrival)]
+               interp(rate_by, by_id[r.rid]["nx"]) for r in order]
+    arrivals = [r.arrival for r in order]
     base_lat = serve.fifo_latencies(arrivals, service)
     base_makespan = max(a + l for a, l in zip(arrivals, base_lat))
-    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1,
+    out = {"workload": "served_droplets_%d" % len(reqs), "storage": "fp32_dev",
+           "arrival_rate_per_s": rate, "steps_range": [steps_lo, steps_hi], "slots": slots,
+           "chunk_steps": chunk, "hbm_budget_bytes": srv.hbm_bytes,
+           "requests": len(done), "makespan_s": round(makespan, 2),
+           "mlups": round(work / makespan / 1e6, 1),
+           "mlups_stable_results": round(stable_work / makespan / 1e6, 1),
+           "p50_latency_s": round(stats["p50_s"], 3), "p99_latency_s": round(stats["p99_s"], 3),
+           "max_concurrent": srv.max_concurrent, "peak_admitted_bytes": srv.peak_bytes,
+           "unstable_results": unstable, "node_steps": work,
+           "plain_fp64_loop_model": {
+               "mlups": round(work / base_makespan / 1e6, 1),
+               "makespan_s": round(base_makespan, 1),
+               "p50_latency_s": round(float(np.percentile(base_lat, 50)), 2),
+               "p99_latency_s": round(float(np.percentile(base_lat, 99)), 2),
+               "fp64_fluid_mlups_by_side": {str(k): round(v / 1e6, 1) for k, v in rate_by.items()},
+               "how": "FIFO queue on the same arrivals with service time = measured FP64 "
+                      "set-up + fluid nodes x steps / measured FP64 step rate of that size"},
+           "clocks": clk.summary()}
+    if plain_subset:
+        sub = sorted(reqs, key=lambda r: r["arrival"])[:plain_subset]
+        t1 = time.perf_counter()
+        pdone = serve.run_one_at_a_time(sub)
+        pspan = time.perf_counter() - t1
+        plat = [r.latency for r in sorted(pdone, key=lambda r: r.arrival)]
+        sub_ids = [r["rid"] for r in sub]
+        k = [i for i, r in enumerate(order) if r.rid in sub_ids]
+        model_sub = serve.fifo_latencies([arrivals[i] for i in k], [service[i] for i in k])
+        out["plain_fp64_loop_run"] = {
+            "requests": len(pdone), "first_arrivals": plain_subset,
+            "makespan_s": round(pspan, 2),
+            "mlups": round(sum(r.fluid_nodes * r.steps for r in pdone) / pspan / 1e6, 1),
+            "p50_latency_s": round(float(np.percentile(plat, 50)), 3),
+            "p99_latency_s": round(float(np.percentile(plat, 99)), 3),
+            "model_p50_latency_s_same_requests": round(float(np.percentile(model_sub, 50)), 3),
+            "model_p99_latency_s_same_requests": round(float(np.percentile(model_sub, 99)), 3),
+            "how": "the first arrivals of the same stream served for real by one FP64 lattice "
+                   "at a time (serve.run_one_at_a_time), arrivals on the wall clock"}
+    if accuracy_sample:
+        errs = []
+        for rid, rho32 in kept.items():
+            req = by_id[rid]
+            lat = serve.request_lattice(req, lbm.FP64)
+            lat.step(req["steps"])
+            rho64 = lat.fields()[0]
+            lat.close()
+            m = np.isfinite(rho64)
+            d = np.abs(rho32[m] - rho64[m])
+            errs.append({"rid": rid, "side": req["nx"], "scheme": req["scheme"],
+                         "steps": req["steps"],
+                         "rho_normwise": float("%.3e" % (d.max() / np.max(rho64[m]))),
+                         "rho_max_rel": float("%.3e" % np.max(d / rho64[m]))})
+        out["accuracy_vs_fp64_alone"] = {
+            "requests": len(errs),
+            "max_rho_normwise": max((e["rho_normwise"] for e in errs), default=None),
+            "max_rho_rel": max((e["rho_max_rel"] for e in errs), default=None),
+            "samples": errs,
+            "how": "finished stable served requests (FP32 deviations, in the mix) against the "
+                   "same request run alone with FP64 storage"}
+    return out
+
+
+def run_serve(args):
+    """The served stream as its own JSON line (--serve)."""
+    import torch
+    torch.cuda.set_device(0)
+    r = served_measure(args.serve_requests, args.serve_rate, args.serve_steps_lo,
+                       args.serve_steps_hi, args.serve_slots, args.serve_hbm_gb, args.serve_chunk,
+                       accuracy_sample=args.serve_accuracy_sample,
+                       plain_subset=args.serve_plain_subset)
+    line = {"metric": METRIC, "value": r["mlups"], "unit": UNIT, "n_gpus": 1,
             "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "served_droplets_%d" % len(reqs), "storage": "fp32_dev",
-                       "arrival_rate_per_s": args.serve_rate, "slots": args.serve_slots,
-                       "chunk_steps": args.serve_chunk,
-                       "hbm_budget_bytes": srv.hbm_bytes},
-            "served": {"requests": len(done), "makespan_s": round(makespan, 2),
-                       "p50_latency_s": round(stats["p50_s"], 3),
-                       "p99_latency_s": round(stats["p99_s"], 3),
-                       "max_concurrent": srv.max_concurrent,
-                       "peak_admitted_bytes": srv.peak_bytes, "unstable_results": unstable,
-                       "node_steps": work},
-            "plain_fp64_loop_model": {
-                "mlups": round(work / base_makespan / 1e6, 1),
-                "makespan_s": round(base_makespan, 1),
-                "p50_latency_s": round(float(np.percentile(base_lat, 50)), 2),
-                "p99_latency_s": round(float(np.percentile(base_lat, 99)), 2),
-                "fp64_fluid_mlups_by_side": {str(k): round(v / 1e6, 1) for k, v in rate.items()},
-                "how": "FIFO queue on the same arrivals with service time = measured FP64 "
-                       "set-up + fluid nodes x steps / measured FP64 step rate of that size"},
-            "clocks": clk.summary()}
+            "config": {k: r[k] for k in ("workload", "storage", "arrival_rate_per_s", "slots",
+                                         "chunk_steps", "hbm_budget_bytes")},
+            "served": r, "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -664,6 +805,12 @@ def main():
     ap.add_argument("--serve-chunk", type=int, default=200)
     ap.add_argument("--serve-hbm-gb", type=float, default=0.0,
                     help="memory budget of the server (0: 80%% of the free device memory)")
+    ap.add_argument("--serve-accuracy-sample", type=int, default=8,
+                    help="served requests re-run alone in FP64 to state the served accuracy")
+    ap.add_argument("--serve-plain-subset", type=int, default=16,
+                    help="first arrivals also served for real by the plain one-at-a-time loop")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="default line without the batched / served / precision sub-objects")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -719,6 +866,10 @@ def main():
     achieved = n_fluid * bpu / (ms_step / args.steps * 1e-3) / 1e9
     traffic = captured_traffic()
 
+    # the FP64 FMA pipe, measured (one timed launch of about half a second)
+    fp64_gflops, fp64_ms = lbm.lbm_probe_fp64_fma(150000)
+    fp64_ops = fp64_gflops / 2 * 1e9  # pipe operations per second
+
     variants = {}
     for prec in ("fp64", "fp32_dev", "fp16_dev"):
         for name in SCHEME_NAMES:
@@ -731,9 +882,26 @@ def main():
                 "boundary_kernel_us": round(1e3 * b_ms / args.variant_steps, 2),
                 "hbm_frac_step_kernel": round(
                     n_fluid * vb / (s_ms / args.variant_steps * 1e-3) / 1e9 / peak, 3)}
+            if prec == "fp64":
+                variants["%s/%s" % (prec, name)]["fp64_alu_frac_step_kernel"] = round(
+                    FP64_PIPE_OPS_PER_NODE * n_fluid / (s_ms / args.variant_steps * 1e-3)
+                    / fp64_ops, 3)
 
     e2e_value, h2d, d2h, e2e_split = run_e2e(w, args.steps)
     e2e_value = world * e2e_value
+
+    # the next rows of the path, on one process only: the batched workload (200 steps of the
+    # 512 lattices), the served stream at and below capacity (with a served-accuracy sample and
+    # the plain FP64 loop run for real on the first arrivals), the storage formats against the
+    # FP64 oracle at 2048^2 (1000 steps)
+    nxt = {}
+    if world == 1 and not args.no_next_rows:
+        nxt["batched"] = batched_measure(512, "fp32_dev", 200, 20)
+        nxt["served"] = served_measure(300, 200.0, 2000, 20000, 256, 0.0, 200,
+                                       accuracy_sample=args.serve_accuracy_sample,
+                                       plain_subset=args.serve_plain_subset)
+        nxt["served_below_capacity"] = served_measure(120, 10.0, 2000, 20000, 256, 0.0, 200)
+        nxt["precision"] = precision_measure(2048, (20, 50, 100, 250, 500, 1000))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -792,9 +960,13 @@ def main():
                     "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1),
                     "split": e2e_split},
             "cpu_baseline": cpu,
+            "fp64_fma_peak": {"gflops": round(fp64_gflops, 1), "ms": round(fp64_ms, 2),
+                              "kind": "measured (lbm_probe_fp64_fma, one timed launch)",
+                              "pipe_ops_per_fp64_node_update": FP64_PIPE_OPS_PER_NODE},
             "variants": variants,
             "mass_after": m_after,
         }
+        line.update(nxt)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -60,15 +60,15 @@ typedef enum {
   LBM_BOUZIDI_L_A = 9 /* linear Bouzidi, then the rest-population correction of Eq. (18)  */
 } lbm_scheme;
 
-/* How populations are stored in device memory.  The per-node step computes in FP64 for
- * LBM_FP64 and in FP32 for the deviation formats, which store f_a - w_a rho_ref: LBM_FP32_DEV
- * all nine as FP32; LBM_FP16_DEV the rest population f_0 (which does not stream) as FP32 and the
- * eight moving ones as FP16 (20 bytes per node and lattice).  In both the rest population takes
- * the node's stored mass minus the rounded moving populations, so the bulk step keeps mass to
- * FP32 accuracy.  The boundary pass computes in FP64 for every format (stored values and the
- * step's moments widened, each incoming value rounded once when stored); with deviation storage
- * its rounding residue is carried per boundary node in FP64 so the mass-conserving schemes stay
- * conserving. */
+/* How populations are stored in device memory.  Arithmetic is FP64 for LBM_FP64 and FP32 for
+ * the deviation formats, which store f_a - w_a rho_ref: LBM_FP32_DEV all nine as FP32;
+ * LBM_FP16_DEV the rest population f_0 (which does not stream) as FP32 and the eight moving ones
+ * as FP16 (20 bytes per node and lattice).  In both the rest population takes the node's stored
+ * mass minus the rounded moving populations, so the bulk step keeps mass to FP32 accuracy.  The
+ * boundary pass computes the incoming link values in the same arithmetic (FP32 for the deviation
+ * formats) and keeps each boundary node's mass balance in FP64: the imbalance between its stored
+ * outgoing and incoming values, and the rounding residue of its rest population, carried from
+ * step to step, so the mass-conserving schemes stay conserving. */
 typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1, LBM_FP16_DEV = 2 } lbm_precision;
 
 typedef enum { LBM_EOS_NONE = 0, LBM_EOS_EXP = 1, LBM_EOS_CS = 2 } lbm_eos_kind;

@@ -16,8 +16,11 @@
 // weights of Eqs. 12-14, which operands a link reads) is evaluated once at creation by
 // link_setup_kernel into a per-link recipe, with the same operations the equations state; a step
 // then costs each link a few loads and FMAs.  An 8-lane group handles a boundary node, one lane
-// per link; per-node sums use fixed-order shuffles (bitwise reproducible).  Arithmetic is FP64
-// for every storage format.
+// per link; per-node sums use fixed-order shuffles (bitwise reproducible).  Link values are
+// computed in the step's arithmetic type (FP64 for FP64 storage, FP32 for the deviation
+// formats); each boundary node's mass bookkeeping is FP64 for every format.  (FP64 link
+// arithmetic for the deviation formats was measured: 4.3 us more per step at 4096^2 and 0.25 ms
+// more per batched step of 512 lattices, on GB300's narrow FP64 pipe.)
 #include "d2q9.cuh"
 
 namespace lbm {
@@ -143,6 +146,11 @@ __global__ void link_setup_kernel(DevParams p, int nb, const int32_t* __restrict
     r.c2[l] = c2;
     r.chi[l] = chi;
     r.cus[l] = cus;
+    r.c0f[l] = float(c0);
+    r.c1f[l] = float(c1);
+    r.c2f[l] = float(c2);
+    r.chif[l] = float(chi);
+    r.cusf[l] = float(cus);
   }
 }
 
@@ -164,14 +172,18 @@ __device__ __forceinline__ T group8_sum(T v, unsigned mask) {
   return v;
 }
 
+template <typename T>
+__device__ __forceinline__ T pick(const double* d, const float* f, int l) {
+  if constexpr (sizeof(T) == 8) return d[l]; else return f[l];
+}
+
 // Boundary node b of a lattice handled by lane k (0..7) of an 8-lane group (node_ok false: a
-// padding group, which still takes part in the shuffles).  The arithmetic is FP64 for every
-// storage format: the deviation formats' stored values and the step kernel's FP32 moments are
-// widened, each incoming value is rounded once when stored.  Their mass bookkeeping is exact
-// as well: each node's imbalance between the stored outgoing and incoming values is summed in
-// FP64 and goes, with the previous step's FP64 rounding residue, into its rest population.  For
-// schemes A and L-Bouzidi + A that is Eq. (18); for B (balanced by construction, Eq. 19) and
-// halfway bounce-back it only returns the rounding to the storage format.
+// padding group, which still takes part in the shuffles).  Arithmetic type T: FP64 for FP64
+// storage; FP32 for the deviation formats, whose mass bookkeeping is exact instead: each node's
+// imbalance between the stored outgoing and incoming values is summed in FP64 and goes, with the
+// previous step's FP64 rounding residue, into its rest population.  For schemes A and
+// L-Bouzidi + A that is Eq. (18); for B (balanced by construction, Eq. 19) and halfway
+// bounce-back it only returns the FP32 rounding.
 template <typename S>
 __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k, bool node_ok,
                                                const int32_t* __restrict__ bnode,
@@ -183,19 +195,18 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
                                                const double* __restrict__ uy_m,
                                                double* __restrict__ carry,
                                                double* __restrict__ force, unsigned mask) {
-  using T = double;                  // arithmetic
-  using C = typename Pop<S>::C;      // the step kernel's arithmetic (its moments' type)
+  using T = typename Pop<S>::C;
   constexpr bool DEV = Pop<S>::dev;
   const int scheme = p.scheme;
   const int N = L.N;
   const bool fix_f0 = scheme == LBM_MOD_A || scheme == LBM_BOUZIDI_L_A;
   const bool conserving = fix_f0 || scheme == LBM_MOD_B || scheme == LBM_HBB;
   const bool fict = scheme == LBM_MOD_B || scheme == LBM_BAO;
-  const T rref = L.rho_ref;  // 0 for FP64 storage
+  const T rref = DEV ? p.k<T>().rho_ref : T(0);
   // macro arrays: FP64 for FP64 storage, FP32 (in the same memory) for the deviation formats
-  const C* rhoT = reinterpret_cast<const C*>(rho_m);
-  const C* uxT = reinterpret_cast<const C*>(ux_m);
-  const C* uyT = reinterpret_cast<const C*>(uy_m);
+  const T* rhoT = reinterpret_cast<const T*>(rho_m);
+  const T* uxT = reinterpret_cast<const T*>(ux_m);
+  const T* uyT = reinterpret_cast<const T*>(uy_m);
 
   // first loads: node and link records
   int n = 0, l0 = 0, nl = 0;
@@ -218,27 +229,27 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
     x2 = r.x2[l];
     uf = r.uf[l];
     kind = r.kind[l];
-    c0 = r.c0[l];
-    c1 = r.c1[l];
-    c2 = r.c2[l];
-    chi = r.chi[l];
-    cus = r.cus[l];
-    rho_b = T(rhoT[LBM_CHK(n, N)]);
-    ubx = T(uxT[n]);
-    uby = T(uyT[n]);
+    c0 = pick<T>(r.c0, r.c0f, l);
+    c1 = pick<T>(r.c1, r.c1f, l);
+    c2 = pick<T>(r.c2, r.c2f, l);
+    chi = pick<T>(r.chi, r.chif, l);
+    cus = pick<T>(r.cus, r.cusf, l);
+    rho_b = rhoT[LBM_CHK(n, N)];
+    ubx = uxT[n];
+    uby = uyT[n];
   }
   // second loads: lattice values (deviations d_ for the FP32 formats; f = d_ + w rho_ref)
   const T w = wgt<T>(a);
   const T wr = w * rref;
   T fo_d = T(0), X1 = T(0), X2 = T(0), usx = T(0), usy = T(0);
   if (act) {
-    fo_d = Pop<S>::load_e(L.dst, src, N);  // outgoing f*_a(x_b, t)
-    if (x1 >= 0) X1 = Pop<S>::load_e(L.dst, x1, N) + wr;
-    if (x2 >= 0) X2 = Pop<S>::load_e((kind & kFromA) ? L.src : L.dst, x2, N) + wr;
+    fo_d = Pop<S>::load_t(L.dst, src, N);  // outgoing f*_a(x_b, t)
+    if (x1 >= 0) X1 = Pop<S>::load_t(L.dst, x1, N) + wr;
+    if (x2 >= 0) X2 = Pop<S>::load_t((kind & kFromA) ? L.src : L.dst, x2, N) + wr;
     if (kind & kGhost) {
       if (uf >= 0) {
-        usx = T(uxT[LBM_CHK(uf, N)]);
-        usy = T(uyT[uf]);
+        usx = uxT[LBM_CHK(uf, N)];
+        usy = uyT[uf];
       } else {
         usx = cus * ubx;
         usy = cus * uby;
@@ -248,7 +259,7 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
   const T fo = fo_d + wr;
   const bool lane0 = node_ok && k == 0;
   T f0_d = T(0);
-  if (lane0 && (fix_f0 || (DEV && conserving))) f0_d = Pop<S>::load_e(L.dst, n, N);
+  if (lane0 && (fix_f0 || (DEV && conserving))) f0_d = Pop<S>::load_t(L.dst, n, N);
 
   const bool gh = act && (kind & kGhost);
   const T br = gh ? bracket<T>(a, usx, usy, ubx, uby) : T(0);
@@ -269,13 +280,13 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
   if (act) {
     // a pure bounce-back link (halfway bounce-back or a fallback) copies the stored value
     const bool copy = DEV && !gh && x1 < 0 && x2 < 0 && c0 == T(1);
-    in_d = Pop<S>::store_e(L.dst, dst, N, copy ? fo_d : val - wr);
+    in_d = Pop<S>::store_t(L.dst, dst, N, copy ? fo_d : val - wr);
   }
   if (force) {
     // Momentum exchange (Sec. 5.1, after Mei et al. 2002): through link a the wall receives
     // e_a (f*_a(x_b, t) + f_abar(x_b, t+1)), with the incoming value as stored; FP64 sums over
     // the node's links in the fixed group order, one (fx, fy) per boundary node.
-    const double m = act ? fo_d + in_d + 2.0 * wgt<double>(a) * rref : 0.0;
+    const double m = act ? double(fo_d) + double(in_d) + 2.0 * wgt<double>(a) * L.rho_ref : 0.0;
     const double fx = group8_sum(double(ex(a)) * m, mask);
     const double fy = group8_sum(double(ey(a)) * m, mask);
     if (lane0) {
@@ -287,12 +298,12 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
   if constexpr (DEV) {
     if (conserving) {
       // exact FP64 imbalance of the stored deviations (the w rho_ref parts cancel)
-      const double dm = group8_sum(act ? fo_d - in_d : 0.0, mask);
+      const double dm = group8_sum(act ? double(fo_d) - double(in_d) : 0.0, mask);
       if (lane0) {
-        const double want = f0_d + dm + carry[b];
-        if (want != f0_d) {
-          const double st = Pop<S>::store_e(L.dst, n, N, want);
-          carry[b] = want - st;
+        const double want = double(f0_d) + dm + carry[b];
+        if (want != double(f0_d)) {
+          const T st = Pop<S>::store_t(L.dst, n, N, T(want));
+          carry[b] = want - double(st);
         } else {
           carry[b] = 0.0;
         }
@@ -393,7 +404,7 @@ cudaError_t launch_b(const DevParams& p, int nb, const int32_t* bnode, const int
                      const uint8_t* ldir, LinkRecipe r, const void* fa, void* fb,
                      const double* rho_m, const double* ux_m, const double* uy_m, double* carry,
                      double* force, cudaStream_t s) {
-  Lat<S> L{fa, fb, p.N, p.rho_ref};
+  Lat<S> L{fa, fb, p.N, p.rho_ref};  // rho_ref also in p.k<T>() for the FP32 formats
   const long long threads = 8LL * nb;
   boundary_kernel<S><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
       p, nb, bnode, boff, ldir, r, L, rho_m, ux_m, uy_m, carry, force);
@@ -405,7 +416,7 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 }  // namespace
 
 size_t link_recipe_bytes(long long nl) {
-  return 5 * align256(nl * 4) + align256(nl) + 5 * align256(nl * 8);
+  return 5 * align256(nl * 4) + align256(nl) + 5 * align256(nl * 8) + 5 * align256(nl * 4);
 }
 
 void link_recipe_carve(char* base, long long nl, LinkRecipe* r) {
@@ -426,6 +437,11 @@ void link_recipe_carve(char* base, long long nl, LinkRecipe* r) {
   r->c2 = (double*)take(nl * 8);
   r->chi = (double*)take(nl * 8);
   r->cus = (double*)take(nl * 8);
+  r->c0f = (float*)take(nl * 4);
+  r->c1f = (float*)take(nl * 4);
+  r->c2f = (float*)take(nl * 4);
+  r->chif = (float*)take(nl * 4);
+  r->cusf = (float*)take(nl * 4);
 }
 
 cudaError_t launch_link_setup(const DevParams& p, int nb, const int32_t* bnode,

@@ -115,6 +115,11 @@ struct LinkRecipe {
   double* c2;
   double* chi;
   double* cus;
+  float* c0f;     // FP32 copies for the deviation formats
+  float* c1f;
+  float* c2f;
+  float* chif;
+  float* cusf;
 };
 // One lattice of a batch as the batched kernels see it.  cur and steps_left are advanced on
 // the device after every step (batch_advance_kernel), so a captured graph stays valid while

@@ -18,21 +18,26 @@ from paper_1908_09235_gb300 import lbm, workloads
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-11
-# FP32 deviation storage with FP32 arithmetic.  Near a steady state the FP32 rounding of each
-# step (~6e-8 relative per operation) repeats instead of averaging out, and the droplet's slowest
-# mode decays too slowly to damp it (a 1e-7 perturbation keeps half its size over 1000 steps), so
-# the error grows about linearly with the number of steps: ~2e-6 normwise after 100 steps,
-# ~2e-5 normwise / ~4e-5 pointwise (vapour, rho_V = 0.034) after 1000.
-#   100 steps:  max |d rho| / max rho <= 1e-5
-#   1000 steps: max |d rho| / max rho <= 5e-5 and max |d rho| / rho <= 1e-4
+# FP32 deviation storage with FP32 arithmetic (100 x 100 droplet against the FP64 oracle).
+# Storage rounding alone (the oracle's FP64 steps with every population rounded to an FP32
+# deviation after each step) accounts for 1.8e-7 normwise after 1000 steps; the rest is the FP32
+# arithmetic of the interface dynamics.  Correctly rounded division, square root and exp, and
+# compensated density and momentum sums, were measured and do not reduce it (1.57e-5, 1.59e-5).
+# Measured with the kernels as they are: relative L2 ||d rho|| / ||rho|| 6.1-6.6e-6 after 1000
+# steps; normwise max |d rho| / max rho 1.05-1.14e-6 after 100 and 1.23-1.38e-5 after 1000;
+# pointwise max |d rho| / rho 2.45-2.86e-5 after 1000 (vapour nodes).
+#   relative L2 after 1000 steps <= 1e-5 (the stated FP32 target, read as a relative norm)
+#   normwise <= 2e-6 after 100 steps and <= 2e-5 after 1000; pointwise <= 4e-5 after 1000
 # FP16 moving populations: each stored population carries one FP16 rounding (2^-11 = 4.9e-4
-# relative), so after 100 steps the normwise error is about one FP16 unit (measured 3.7-4.2e-4);
-# like the FP32 rounding it repeats near a steady state and grows to 0.6-3.8e-3 after 1000 steps.
-TOL16_NORM_100 = 2e-3
-TOL16_NORM_1000 = 1e-2
-TOL32_NORM_100 = 1e-5
-TOL32_NORM_1000 = 5e-5
-TOL32_POINT_1000 = 1e-4
+# relative); normwise 3.2-4.3e-4 after 100 steps, 0.6-4.1e-3 after 1000 (relative L2 up to
+# 2.1e-3).
+TOL16_NORM_100 = 1e-3
+TOL16_NORM_1000 = 8e-3
+TOL16_L2_1000 = 4e-3
+TOL32_NORM_100 = 2e-6
+TOL32_NORM_1000 = 2e-5
+TOL32_POINT_1000 = 4e-5
+TOL32_L2_1000 = 1e-5
 
 
 # ---- geometry: flags and link list bit-exact ----------------------------------------------------
@@ -220,11 +225,14 @@ def test_unstable_run_reports_status(gpu_lib):
 
 # ---- FP32 deviation storage --------------------------------------------------------------------
 def _fp32_errors(lat, s):
+    """(normwise max|d rho| / max rho, pointwise max |d rho| / rho, relative L2
+    ||d rho|| / ||rho||) of the GPU density against the oracle's, over fluid nodes."""
     rg, _, _ = lat.fields()
     ro, _, _ = s.fields()
     m = np.isfinite(ro)
     d = np.abs(rg[m] - ro[m])
-    return float(np.max(d) / np.max(ro[m])), float(np.max(d / ro[m]))
+    return (float(np.max(d) / np.max(ro[m])), float(np.max(d / ro[m])),
+            float(np.linalg.norm(d) / np.linalg.norm(ro[m])))
 
 
 @pytest.mark.parametrize("scheme", [lbm.MOD_A, lbm.MOD_B, lbm.MLS, lbm.HBB])
@@ -235,19 +243,22 @@ def test_droplet_on_cylinder_fp32_dev(gpu_lib, scheme):
     m0 = lat.mass()
     lat.step(100)
     s.step(100)
-    norm100, point100 = _fp32_errors(lat, s)
+    norm100, point100, l2_100 = _fp32_errors(lat, s)
     lat.step(900)
     s.step(900)
-    norm, point = _fp32_errors(lat, s)
+    norm, point, l2 = _fp32_errors(lat, s)
     print("fp32_dev scheme %d: rho error normwise %.3e (100 steps) %.3e (1000), pointwise %.3e "
-          "(100) %.3e (1000)" % (scheme, norm100, norm, point100, point))
+          "(100) %.3e (1000), relative L2 %.3e (100) %.3e (1000)"
+          % (scheme, norm100, norm, point100, point, l2_100, l2))
     assert norm100 <= TOL32_NORM_100, norm100
+    assert l2 <= TOL32_L2_1000, l2
     assert norm <= TOL32_NORM_1000, norm
     assert point <= TOL32_POINT_1000, point
     if scheme in (lbm.MOD_A, lbm.MOD_B, lbm.HBB):
-        # the boundary pass conserves exactly in FP64 (rounding residue carried) and the bulk
-        # collision keeps each node's stored mass; what remains is rounding of stored values
-        assert abs(lat.mass() / m0 - 1) < 1e-6
+        # the boundary pass keeps each node's balance in FP64 (rounding residue carried) and the
+        # bulk collision keeps each node's stored mass; what remains is rounding of stored values
+        # (measured 2.6e-10 - 5.3e-9 after 1000 steps)
+        assert abs(lat.mass() / m0 - 1) < 2e-8
     lat.close()
 
 
@@ -337,14 +348,16 @@ def test_droplet_on_cylinder_fp16_dev(gpu_lib, scheme):
     m0 = lat.mass()
     lat.step(100)
     s.step(100)
-    norm100, point100 = _fp32_errors(lat, s)
+    norm100, point100, l2_100 = _fp32_errors(lat, s)
     lat.step(900)
     s.step(900)
-    norm, point = _fp32_errors(lat, s)
+    norm, point, l2 = _fp32_errors(lat, s)
     print("fp16_dev scheme %d: rho error normwise %.3e (100 steps) %.3e (1000), pointwise %.3e "
-          "(100) %.3e (1000)" % (scheme, norm100, norm, point100, point))
+          "(100) %.3e (1000), relative L2 %.3e (100) %.3e (1000)"
+          % (scheme, norm100, norm, point100, point, l2_100, l2))
     assert norm100 <= TOL16_NORM_100, norm100
     assert norm <= TOL16_NORM_1000, norm
+    assert l2 <= TOL16_L2_1000, l2
     if scheme in (lbm.MOD_A, lbm.MOD_B):
         # the FP32 rest population absorbs the FP16 rounding of the moving populations
         assert abs(lat.mass() / m0 - 1) < 1e-6
@@ -373,8 +386,9 @@ def test_large_droplet_on_cylinder_full_size(gpu_lib, precision):
         m = np.isfinite(o[0])
         rel = float(np.max(np.abs(g[0][m] - o[0][m]) / o[0][m]))
         print("full size, precision %d, 3 steps: pointwise rho error %.3e" % (precision, rel))
-        tol = TOL32_NORM_100 if precision == lbm.FP32_DEV else TOL16_NORM_100
-        assert rel <= tol, rel  # three steps
+        # three steps: a few roundings of the storage format per population
+        tol = 1e-5 if precision == lbm.FP32_DEV else 2e-3
+        assert rel <= tol, rel
     lat.close()
 
 
@@ -391,5 +405,7 @@ def test_reduced_precision_mass_at_8192(gpu_lib, precision):
     m0 = lat.mass()
     lat.step(200)
     # scheme B conserves mass; the FP64 wall-pass bookkeeping keeps the stored total to round-off
-    assert abs(lat.mass() / m0 - 1.0) < 1e-8
+    drift = abs(lat.mass() / m0 - 1.0)
+    print("8192^2, precision %d, 200 steps: mass drift %.3e" % (precision, drift))
+    assert drift < 1e-8
     lat.close()
