@@ -887,7 +887,10 @@ def main():
                     FP64_PIPE_OPS_PER_NODE * n_fluid / (s_ms / args.variant_steps * 1e-3)
                     / fp64_ops, 3)
 
-    e2e_value, h2d, d2h, e2e_split = run_e2e(w, args.steps)
+    # one end-to-end job through the C ABI: upload, at least 400 steps, download (a job of the
+    # timed K steps alone would, at the driver's K = 20, mostly measure the two transfers)
+    e2e_steps = max(args.steps, 400)
+    e2e_value, h2d, d2h, e2e_split = run_e2e(w, e2e_steps)
     e2e_value = world * e2e_value
 
     # the next rows of the path, on one process only: the batched workload (200 steps of the
@@ -958,7 +961,7 @@ def main():
             "clocks": clk.summary(),
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
                     "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1),
-                    "split": e2e_split},
+                    "job_steps": e2e_steps, "split": e2e_split},
             "cpu_baseline": cpu,
             "fp64_fma_peak": {"gflops": round(fp64_gflops, 1), "ms": round(fp64_ms, 2),
                               "kind": "measured (lbm_probe_fp64_fma, one timed launch)",
