@@ -268,8 +268,11 @@ def run_e2e(w, steps):
     host[2].numpy()[:] = np.nan_to_num(uy.ravel())
     out = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)]
     lib = lbm.load_library()
-    # one-time set-up outside the timed region: the context's captured graph of steps (it stays
-    # valid across lbm_init_fields while rho_ref is unchanged)
+    # one-time set-up outside the timed region: the same upload once (it fixes the automatic
+    # rho_ref from this state) and the context's captured graph of steps, which stays valid
+    # across lbm_init_fields while rho_ref is unchanged
+    lbm._check(lat.ctx, lib.lbm_init_fields(lat.ctx, host[0].data_ptr(), host[1].data_ptr(),
+                                            host[2].data_ptr()))
     lat.step(32)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
