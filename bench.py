@@ -956,7 +956,7 @@ def main():
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "step_vec_kernel (fused force+collision+stream, "
-                                   "16-byte population vectors)",
+                                   "16-byte population vectors, psi ring rows by TMA)",
                          "bytes_per_fluid_update": bpu},
             "step_kernel_us": round(1e3 * ms_step / args.steps, 2),
             "boundary_kernel_us": round(1e3 * ms_bnd / args.steps, 2),

@@ -127,12 +127,17 @@ typedef struct {
   int32_t kernel_path; /* step kernel, all with the same results bit for bit:                  *
                         * 0: the fastest measured: for FP32/FP16 deviations with nx % 4 == 0    *
                         *    and ny >= 8 (FP16: 12) the vectorised kernel (population vectors   *
-                        *    of 16 B, halo staged by cp.async), otherwise the scalar tiles;      *
+                        *    of 16 B; the two psi-ring rows of tiles away from the x seam staged *
+                        *    by tensor copies (TMA), the rest of the halo by cp.async), otherwise *
+                        *    the scalar tiles; a copy wait that expires is reported as           *
+                        *    LBM_ETIMEOUT by lbm_mass;                                           *
                         * 1: the scalar tile kernel (one node per thread and row);              *
                         * 2: FP32 deviations on lattices with nx % 16 == 0, nx, ny >= 64: a     *
                         *    persistent kernel that stages tiles by TMA; otherwise as 0;         *
                         * 3: the vectorised kernel wherever nx % 4 == 0 (FP64: nx % 2 == 0) and *
-                        *    ny >= 8 (FP16: 12), FP64 included; otherwise the scalar tiles       */
+                        *    ny >= 8 (FP16: 12), FP64 included, its halo staged by cp.async     *
+                        *    only; otherwise the scalar tiles;                                   *
+                        * 4: the same as 0                                                       */
   int32_t track_force; /* nonzero: the wall pass records the momentum exchange for lbm_force   *
                         * (also switched on by lbm_set_inflow); off by default, it costs the   *
                         * wall pass a few microseconds per step; ignored by batches            */

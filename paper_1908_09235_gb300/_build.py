@@ -30,7 +30,7 @@ def _nvcc():
 
 
 def _sources():
-    names = CUDA_SOURCES + CXX_SOURCES + ["d2q9.cuh", "step_core.cuh", "lbm_internal.h"]
+    names = CUDA_SOURCES + CXX_SOURCES + ["d2q9.cuh", "step_core.cuh", "tma.cuh", "lbm_internal.h"]
     paths = [os.path.join(CSRC, n) for n in names]
     paths.append(os.path.join(os.path.dirname(HERE), "include", "lbm_gb300.h"))
     paths.append(os.path.abspath(__file__))

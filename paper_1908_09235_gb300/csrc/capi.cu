@@ -84,7 +84,7 @@ cudaError_t launch_bulk(lbm_ctx* c, cudaStream_t s, int cur) {
     return launch_step_tma(c->tmap[cur], c->fmap, c->p, c->f[cur], c->f[1 - cur], c->flags,
                            c->rho_m, c->ux_m, c->uy_m, c->err_flag, s);
   return launch_step(c->precision, c->p, c->f[cur], c->f[1 - cur], c->flags, c->rho_m, c->ux_m,
-                     c->uy_m, false, s, c->kernel_path);
+                     c->uy_m, false, s, c->kernel_path, c->err_flag);
 }
 
 lbm_status launch_one_step(lbm_ctx* c, cudaStream_t s, int cur) {

@@ -88,15 +88,20 @@ cudaError_t launch_geom_emit(const GeomParams& g, uint8_t* flags, const int2* bl
 // step_vec_width(precision) and ny at least its tile height (8; FP16: 12).
 int step_vec_width(int precision);
 bool step_vec_supported(int precision, int nx, int ny);
+// tma_ring (FP32 deviations, not fields_only): the two rows of the psi ring are staged by tensor
+// copies instead of per-thread cp.async (tiles away from the x seam); an expired wait sets
+// kErrTimeout in *err
 cudaError_t launch_step_vec(int precision, const DevParams& p, const void* fa, void* fb,
                             const uint8_t* flags, double* rho_m, double* ux_m, double* uy_m,
-                            bool fields_only, cudaStream_t s);
+                            bool fields_only, cudaStream_t s, bool tma_ring = false,
+                            int* err = nullptr);
 // path: 0 = the vectorised kernel for the deviation formats where step_vec_supported(), else
 // the scalar tile kernel; 1 = the scalar tile kernel; 3 = the vectorised kernel where
-// step_vec_supported() (FP64 too)
+// step_vec_supported() (FP64 too), its psi ring staged by cp.async only; 4 = as 0.  Paths 0 and
+// 4 stage the deviation kernels' psi-ring rows by tensor copies where a tile allows (needs err)
 cudaError_t launch_step(int precision, const DevParams& p, const void* fa, void* fb,
                         const uint8_t* flags, double* rho_m, double* ux_m, double* uy_m,
-                        bool fields_only, cudaStream_t s, int path = 0);
+                        bool fields_only, cudaStream_t s, int path = 0, int* err = nullptr);
 
 // boundary.cu
 // Per-link recipe of the wall pass, fixed at creation (depends on q, tau and the scheme only):
@@ -190,6 +195,9 @@ bool tma_step_supported(int precision, int nx, int ny);
 cudaError_t launch_wait_selftest(unsigned long long limit_ns, int arrive, int* out,
                                  cudaStream_t s);
 bool make_lattice_tensor_map(void* map, const void* base, int nx, int ny);
+bool make_ring_tensor_map(void* map, const void* base, int nx, int ny, int box_w);
+bool make_ring_tensor_maps_fp16(void* map0, void* map1, const void* base, int nx, int ny, int w0,
+                                int w1);
 bool make_flags_tensor_map(void* map, const void* base, int nx, int ny);
 cudaError_t launch_step_tma(const void* map, const void* flag_map, const DevParams& p,
                             const void* fa, void* fb, const uint8_t* flags, double* rho_m,

@@ -173,11 +173,12 @@ cudaError_t launch_batch_step(int precision, int eos, int ry, const BatchDomain*
 
 cudaError_t launch_step(int precision, const DevParams& p, const void* fa, void* fb,
                         const uint8_t* flags, double* rho_m, double* ux_m, double* uy_m,
-                        bool fields_only, cudaStream_t s, int path) {
+                        bool fields_only, cudaStream_t s, int path, int* err) {
   // FP64 is bound by the FP64 pipe, where the scalar tiling (fewer ring psi per node) is faster
-  const bool vec = path == 3 || (path == 0 && precision != LBM_FP64);
+  const bool vec = path == 3 || ((path == 0 || path == 4) && precision != LBM_FP64);
   if (vec && step_vec_supported(precision, p.nx, p.ny))
-    return launch_step_vec(precision, p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
+    return launch_step_vec(precision, p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s,
+                           (path == 0 || path == 4) && err != nullptr, err);
   if (precision == LBM_FP32_DEV)
     return launch_s<float>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
   if (precision == LBM_FP16_DEV)

@@ -12,12 +12,14 @@
 #include <cudaTypedefs.h>
 
 #include "step_core.cuh"
+#include "tma.cuh"
 
 namespace lbm {
 
 namespace {
 
 using namespace step_core;
+using namespace tma;
 
 constexpr int TYM = 16;                   // threads of a CTA in y (512 threads)
 constexpr int RYT = 2;                    // rows per thread: tile 32 x 32
@@ -35,78 +37,6 @@ constexpr uint32_t STAGE_BYTES = POP_BYTES + FLAG_BYTES;  // bytes the copies br
 constexpr uint32_t STAGE_STRIDE = (FLAG_OFF + FLAG_BYTES + 127) / 128 * 128;
 constexpr int NSTAGE = 2;
 constexpr size_t SMEM_BYTES = NSTAGE * STAGE_STRIDE + (TH + 2) * (TX + 2) * 4;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of one mbarrier wait
-
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(saddr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait for the given phase of a stage's barrier; false after about limit_ns (and after
-// 2^32 polls whatever the clock says).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  unsigned long long limit_ns = kWaitNs) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (long long i = 0; i < (1LL << 32); ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 0 && global_ns() - t0 > limit_ns) return false;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(saddr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(saddr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
 
 // A tile whose staged boxes lie inside the lattice (no periodic wrap): copied by TMA.
 __device__ __forceinline__ bool tma_tile(int x0, int y0, int nx, int ny) {
@@ -334,6 +264,50 @@ bool make_flags_tensor_map(void* map, const void* base, int nx, int ny) {
                   const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Tensor map of one FP32 lattice for the vector step kernel's psi ring: dims (nx, ny, 9), box
+// box_w x 1 x 9 (one staged row of all nine planes).
+bool make_ring_tensor_map(void* map, const void* base, int nx, int ny, int box_w) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)box_w, 1, 9};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                  const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Tensor maps of one FP16-deviation lattice for the vector step kernel's psi ring: map0 the FP32
+// rest plane (dims (nx, ny), box w0 x 1), map1 the eight FP16 planes after it (dims (nx, ny, 8),
+// box w1 x 1 x 8).  The FP16 row pitch must be a multiple of 16 bytes (nx % 8 == 0).
+bool make_ring_tensor_maps_fp16(void* map0, void* map1, const void* base, int nx, int ny, int w0,
+                                int w1) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+  if (!fn || nx % 8 != 0) return false;
+  const cuuint64_t d0[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  const cuuint64_t s0[1] = {(cuuint64_t)nx * 4};
+  const cuuint32_t b0[2] = {(cuuint32_t)w0, 1};
+  const cuuint32_t e0[2] = {1, 1};
+  CUresult r = fn(static_cast<CUtensorMap*>(map0), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void*>(base), d0, s0, b0, e0, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  const size_t N = (size_t)nx * ny;
+  void* moving = static_cast<char*>(const_cast<void*>(base)) + N * 4;
+  const cuuint64_t d1[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 8};
+  const cuuint64_t s1[2] = {(cuuint64_t)nx * 2, (cuuint64_t)N * 2};
+  const cuuint32_t b1[3] = {(cuuint32_t)w1, 1, 8};
+  const cuuint32_t e1[3] = {1, 1, 1};
+  r = fn(static_cast<CUtensorMap*>(map1), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, moving, d1, s1, b1,
+         e1, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 

@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "step_core.cuh"
+#include "tma.cuh"
 
 namespace lbm {
 
@@ -60,6 +61,14 @@ struct Vec<float> {
   static constexpr int ES = 4;  // largest element size in bytes
   static constexpr int VH = 8;  // warps per CTA = rows per tile
   static constexpr int kBlocks = 3;
+  // a staged ring row: 9 planes of SWE elements (x0 - V .. x0 + 32 V + V - 1), plane a at
+  // ring_off(a); a tensor copy brings kTmaWidth columns from x0 - kTmaLeft
+  static constexpr int SWE = VW * V + 2 * V;
+  static constexpr int kTmaLeft = V, kTmaWidth = SWE;
+  template <bool TMA>
+  __host__ __device__ static constexpr int ring_row_bytes() { return 9 * SWE * ES; }
+  template <bool TMA>
+  static __device__ __forceinline__ int ring_off(int a) { return a * SWE * ES; }
   static __device__ __forceinline__ const float* at(const void* b, int a, int N, int n) {
     return static_cast<const float*>(b) + a * N + LBM_CHK(n, N - 3);
   }
@@ -93,6 +102,12 @@ struct Vec<double> {
   static constexpr int ES = 8;
   static constexpr int VH = 8;
   static constexpr int kBlocks = 2;
+  static constexpr int SWE = VW * V + 2 * V;
+  static constexpr int kTmaLeft = V, kTmaWidth = SWE;
+  template <bool TMA>
+  __host__ __device__ static constexpr int ring_row_bytes() { return 9 * SWE * ES; }
+  template <bool TMA>
+  static __device__ __forceinline__ int ring_off(int a) { return a * SWE * ES; }
   static __device__ __forceinline__ const double* at(const void* b, int a, int N, int n) {
     return static_cast<const double*>(b) + a * N + LBM_CHK(n, N - 1);
   }
@@ -131,6 +146,22 @@ struct Vec<__half> {
   // ran 3% faster than with 8 rows, the FP32 step 7% slower
   static constexpr int VH = 12;
   static constexpr int kBlocks = 2;
+  // a staged ring row (ring_off(a): element x0 - V of plane a).  Staged by cp.async: 9 plane
+  // regions of SWE 4-byte slots.  Staged by tensor copies (TMA): the FP32 rest plane (SWE
+  // floats from x0 - V) at 0, then the eight FP16 planes densely, kTmaWidth halves each from
+  // x0 - 8 (16-byte aligned), from the next 128-byte boundary on.
+  static constexpr int SWE = VW * V + 2 * V;
+  static constexpr int kTmaLeft = 8, kTmaWidth = SWE + 8;
+  static constexpr int kMovOff = (SWE * 4 + 127) / 128 * 128;
+  template <bool TMA>
+  __host__ __device__ static constexpr int ring_row_bytes() { return TMA ? kMovOff + 8 * kTmaWidth * 2 : 9 * SWE * ES; }
+  template <bool TMA>
+  static __device__ __forceinline__ int ring_off(int a) {
+    if constexpr (TMA)
+      return a == 0 ? 0 : kMovOff + (a - 1) * kTmaWidth * 2 + (kTmaLeft - V) * 2;
+    else
+      return a * SWE * ES;
+  }
   static __device__ __forceinline__ const __half* moving(const void* b, int a, int N, int n) {
     return reinterpret_cast<const __half*>(static_cast<const float*>(b) + N) + (a - 1) * N +
            LBM_CHK(n, N);
@@ -201,11 +232,18 @@ __device__ __forceinline__ void load_flags(const uint8_t* flags, int n, uint8_t 
   }
 }
 
-template <typename S, int EOS, bool FIELDS>
+// TR: the two ring rows of tiles away from the x seam are staged by tensor copies
+// (cp.async.bulk.tensor) issued by one thread, instead of cp.async by every lane: FP32 one copy
+// per row (rmap, box SWE x 1 x 9); FP16 two (rmap: the FP32 rest plane, box SWE x 1; rmap2: the
+// eight FP16 planes, box kTmaWidth x 1 x 8).  Their wait is bounded (an expired wait sets
+// kErrTimeout in *err).
+template <typename S, int EOS, bool FIELDS, bool TR>
 __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
     step_vec_kernel(DevParams p, const void* __restrict__ fa, void* __restrict__ fb,
                     const uint8_t* __restrict__ flags, double* __restrict__ rho_m,
-                    double* __restrict__ ux_m, double* __restrict__ uy_m) {
+                    double* __restrict__ ux_m, double* __restrict__ uy_m,
+                    const __grid_constant__ CUtensorMap rmap,
+                    const __grid_constant__ CUtensorMap rmap2, int* __restrict__ err) {
   using C = typename Pop<S>::C;
   using VT = Vec<S>;
   constexpr int V = VT::V;
@@ -215,9 +253,11 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
   constexpr int ES = VT::ES;
   constexpr bool DEV = Pop<S>::dev;
   constexpr bool PSI = EOS != LBM_EOS_NONE;
-  // staged populations: the two ring rows, and the side vectors (x0 - V, x0 + V nv) of the own
-  // rows; plane regions sized for the largest element
-  __shared__ __align__(16) unsigned char ring_st[PSI ? 2 * 9 * SW * ES : 16];
+  // staged populations: the two ring rows (each 9 plane rows of SW elements, rows 128-byte
+  // aligned for the tensor copies), and the side vectors (x0 - V, x0 + V nv) of the own rows;
+  // plane regions sized for the largest element
+  constexpr int RS = (VT::template ring_row_bytes<TR>() + 127) / 128 * 128;
+  __shared__ __align__(128) unsigned char ring_st[PSI ? 2 * RS : 16];
   __shared__ __align__(16) unsigned char side_st[PSI ? VH * 2 * 9 * V * ES : 16];
   // psi of x0 - V + j, rows y0 - 1 .. y0 + VH, at column pj(j) = j + j / V: one pad element after
   // every V, so lane l's nodes and their x-neighbours sit at fixed offsets -2, 0 .. V - 1, V + 1
@@ -236,6 +276,36 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
   // one wrap suffices: nx >= V and ny >= VH (checked by the launcher)
   auto wrapx = [nx](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
   auto wrapy = [ny](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
+
+  // tensor copies of the ring rows: a whole tile whose staged columns x0 - V .. x0 + TW + V - 1
+  // lie inside the lattice (no wrap in x; rows are addressed wrapped)
+  __shared__ __align__(8) uint64_t ring_bar;
+  bool tma_rows = false;
+  if constexpr (TR && PSI) {
+    tma_rows = x0 >= VT::kTmaLeft && x0 - VT::kTmaLeft + VT::kTmaWidth <= nx;
+    if (tma_rows) {  // uniform over the CTA
+      if (tid == 0) {
+        tma::mbar_init(&ring_bar, 1);
+        tma::fence_mbar_init();
+      }
+      __syncthreads();
+      if (tid == 0) {
+        if constexpr (sizeof(S) == 2) {
+          tma::mbar_expect_tx(&ring_bar, 2u * (SW * 4u + 8u * VT::kTmaWidth * 2u));
+          for (int r = 0; r < 2; ++r) {
+            const int yr = wrapy(r == 0 ? y0 - 1 : y0 + VH);
+            tma::tma_load_2d(ring_st + r * RS, &rmap, &ring_bar, x0 - V, yr);
+            tma::tma_load_3d(ring_st + r * RS + VT::kMovOff, &rmap2, &ring_bar,
+                             x0 - VT::kTmaLeft, yr, 0);
+          }
+        } else {
+          tma::mbar_expect_tx(&ring_bar, 2u * 9u * SW * ES);
+          tma::tma_load_3d(ring_st, &rmap, &ring_bar, x0 - V, wrapy(y0 - 1), 0);
+          tma::tma_load_3d(ring_st + RS, &rmap, &ring_bar, x0 - V, wrapy(y0 + VH), 0);
+        }
+      }
+    }
+  }
 
   // ---- staged copies: ring rows (slot s at x0 + V (s - 1), s = 0 .. nv + 1) and the side
   // vectors (x0 - V, x0 + V nv) of the own rows.  Warp w copies the ring's (row, plane) pairs
@@ -256,10 +326,10 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int c = w + VH * i;  // ring row r = c / 9, plane a = c % 9
-      if (c < 18) {
+      if (c < 18 && !tma_rows) {
         const int r = c >= 9 ? 1 : 0, a = c - 9 * r;
         const int grow = wrapy(r == 0 ? y0 - 1 : y0 + VH) * nx;
-        unsigned char* plane = ring_st + c * SW * ES;
+        unsigned char* plane = ring_st + r * RS + VT::template ring_off<TR>(a);
         const int vb = VT::bytes(a);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -353,6 +423,14 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
   if constexpr (PSI) {
     cp_async_wait_all();
     __syncthreads();  // staged populations visible
+    if constexpr (TR) {
+      // every thread observes the tensor copies' completion (which makes their data visible
+      // to it); a wait that expires is reported, and waited out once more with a short bound
+      if (tma_rows && !tma::mbar_wait_bounded(&ring_bar, 0)) {
+        if (tid == 0) atomicOr(err, kErrTimeout);
+        tma::mbar_wait_bounded(&ring_bar, 0, 100000000ull);
+      }
+    }
     // psi of the ring and side nodes from the staged populations
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -364,7 +442,7 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
           const int r = q / RJ, c = q - r * RJ;
           if (c >= rj) continue;
           j = V - 1 + c;  // x0 - V + j; staged ring slots hold the same columns
-          base = ring_st + r * 9 * SW * ES;
+          base = ring_st + r * RS;
           prow = r == 0 ? 0 : VH + 1;
           pcol = j;
         } else {
@@ -374,10 +452,11 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
           prow = row + 1;
           pcol = side == 0 ? V - 1 : V * (nv + 1);
         }
-        const int pstride = q < 2 * RJ ? SW * ES : V * ES;
+        const bool ringq = q < 2 * RJ;
         C g[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) g[a] = VT::staged(base + a * pstride, a, j);
+        for (int a = 0; a < 9; ++a)
+          g[a] = VT::staged(base + (ringq ? VT::template ring_off<TR>(a) : a * V * ES), a, j);
         uint8_t nf = qfl[i];
         if constexpr (SFL) {
           if (q < 2 * RJ)
@@ -508,28 +587,49 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
 template <typename S, int EOS>
 cudaError_t launch_vec_t(const DevParams& p, const void* fa, void* fb, const uint8_t* flags,
                          double* rho_m, double* ux_m, double* uy_m, bool fields_only,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool tma_ring, int* err) {
   constexpr int TW = VW * Vec<S>::V, VH = Vec<S>::VH;
   dim3 block(VW, VH);
   dim3 grid((p.nx + TW - 1) / TW, (p.ny + VH - 1) / VH);
+  CUtensorMap map{}, map2{};  // unused by the kernels without tensor copies
+  if constexpr (!std::is_same<S, double>::value && EOS != LBM_EOS_NONE) {
+    bool maps = tma_ring && !fields_only && err;
+    if (maps) {
+      if constexpr (std::is_same<S, float>::value)
+        maps = make_ring_tensor_map(&map, fa, p.nx, p.ny, Vec<S>::kTmaWidth);
+      else
+        maps = make_ring_tensor_maps_fp16(&map, &map2, fa, p.nx, p.ny, Vec<S>::SWE,
+                                          Vec<S>::kTmaWidth);
+    }
+    if (maps) {
+      step_vec_kernel<S, EOS, false, true>
+          <<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, err);
+      return cudaGetLastError();
+    }
+  }
   if (fields_only)
-    step_vec_kernel<S, EOS, true><<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m);
+    step_vec_kernel<S, EOS, true, false>
+        <<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, err);
   else
-    step_vec_kernel<S, EOS, false><<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m);
+    step_vec_kernel<S, EOS, false, false>
+        <<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, err);
   return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_vec_s(const DevParams& p, const void* fa, void* fb, const uint8_t* flags,
                          double* rho_m, double* ux_m, double* uy_m, bool fields_only,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool tma_ring, int* err) {
   switch (p.eos) {
     case LBM_EOS_EXP:
-      return launch_vec_t<S, LBM_EOS_EXP>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
+      return launch_vec_t<S, LBM_EOS_EXP>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s,
+                                          tma_ring, err);
     case LBM_EOS_CS:
-      return launch_vec_t<S, LBM_EOS_CS>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
+      return launch_vec_t<S, LBM_EOS_CS>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s,
+                                         tma_ring, err);
     default:
-      return launch_vec_t<S, LBM_EOS_NONE>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
+      return launch_vec_t<S, LBM_EOS_NONE>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s,
+                                           tma_ring, err);
   }
 }
 
@@ -546,12 +646,14 @@ bool step_vec_supported(int precision, int nx, int ny) {
 
 cudaError_t launch_step_vec(int precision, const DevParams& p, const void* fa, void* fb,
                             const uint8_t* flags, double* rho_m, double* ux_m, double* uy_m,
-                            bool fields_only, cudaStream_t s) {
+                            bool fields_only, cudaStream_t s, bool tma_ring, int* err) {
   if (precision == LBM_FP32_DEV)
-    return launch_vec_s<float>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
+    return launch_vec_s<float>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s, tma_ring,
+                               err);
   if (precision == LBM_FP16_DEV)
-    return launch_vec_s<__half>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
-  return launch_vec_s<double>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s);
+    return launch_vec_s<__half>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s, tma_ring,
+                                err);
+  return launch_vec_s<double>(p, fa, fb, flags, rho_m, ux_m, uy_m, fields_only, s, false, err);
 }
 
 }  // namespace lbm

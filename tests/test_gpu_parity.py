@@ -299,6 +299,23 @@ def test_vector_step_equals_scalar_tiles(gpu_lib, precision, shape):
     assert a[1] == b[1]
 
 
+# The vector kernels with their psi ring rows staged by tensor copies (the default path).  FP32:
+# 512 and 516 wide hold tiles copied by TMA (x0 - 4 >= 0, x0 + 132 <= nx) beside seam tiles and,
+# at 516, a last tile one vector wide, which stage by cp.async; 256 wide has seam tiles only.
+# FP16 (x0 - 8 >= 0, x0 + 136 <= nx, nx % 8 == 0): 512 and 520 mix both kinds of tile; 516 is
+# not a multiple of 8, so every tile stages by cp.async.
+@pytest.mark.parametrize("precision,shape", [
+    (lbm.FP32_DEV, (512, 64)), (lbm.FP32_DEV, (516, 40)), (lbm.FP32_DEV, (256, 192)),
+    (lbm.FP16_DEV, (512, 64)), (lbm.FP16_DEV, (520, 40)), (lbm.FP16_DEV, (516, 40))])
+def test_tma_ring_step_equals_scalar_tiles(gpu_lib, precision, shape):
+    nx, ny = shape
+    a = _two_phase(nx, ny, precision, 4, 150)
+    b = _two_phase(nx, ny, precision, 1, 150)
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(np.nan_to_num(x, nan=-7.0), np.nan_to_num(y, nan=-7.0))
+    assert a[1] == b[1]
+
+
 @pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_DEV])
 def test_vector_step_single_phase_body_force(gpu_lib, precision):
     # no psi stencil: the vector kernel collides its side nodes from global memory
