@@ -9,8 +9,9 @@
 //
 // psi stencil: psi of the tile's own nodes comes from the lanes' registers; psi of the one-node
 // ring around the tile (the rows above and below, one column on each side) comes from
-// populations staged in shared memory by cp.async, which needs no registers and fetches the side
-// columns as aligned vectors instead of single-element loads.
+// populations staged in shared memory, which needs no registers and fetches the side columns as
+// aligned vectors instead of single-element loads: the two rows by tensor copies where the tile
+// allows (TR), otherwise, and the side columns always, by cp.async.
 //
 // Streaming is push (f*_a of node x goes to x + e_a of the destination lattice, into solid nodes
 // too, whose slots then hold the outgoing populations the wall pass reads).  A population moving
