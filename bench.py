@@ -550,13 +550,15 @@ def _batch_member(lbm, w):
                            droplet=tuple(w["drop"]) + (rl, rv))
 
 
-def batched_measure(n_domains, precision, steps, warmup, base_count=16):
+def batched_measure(n_domains, precision, steps, warmup, base_count=16, accuracy_sample=4):
     """The batched workload (n_domains uneven droplet-on-cylinder lattices, sides 64..512,
     seeded) in one batch: one set of launches per time step under a CUDA graph, tile height and
     tile-queue schedule chosen by the batch's tuner; `steps` timed steps of every lattice.
     Throughput over all lattices and over the lattices that stayed finite (a diverged lattice
     costs the same per step but its result is void), beside the plain loop that advances one
-    FP64 lattice at a time (the first base_count lattices, 10 steps each)."""
+    FP64 lattice at a time (the first base_count lattices, 10 steps each), and the density of
+    accuracy_sample finite lattices against the same lattice run alone in FP64."""
+    import numpy as np
     import torch
 
     from paper_1908_09235_gb300 import lbm, workloads
@@ -584,6 +586,27 @@ def batched_measure(n_domains, precision, steps, warmup, base_count=16):
             finite_nodes += lbm.lbm_info(b.ctx(s_))["n_fluid"]
         except lbm.LBMError:
             unstable.append(w["name"])
+    # accuracy: a few finite lattices, spread over the workload, against the same lattice run
+    # alone with FP64 storage for the same number of steps
+    total = warmup + steps + 5
+    acc = []
+    for k in range(0, len(ws), max(1, len(ws) // accuracy_sample) if accuracy_sample else len(ws) + 1):
+        if len(acc) >= accuracy_sample or ws[k]["name"] in unstable:
+            continue
+        rho_b = b.fields(slots[k])[0]
+        w = ws[k]
+        eos = lbm.make_eos(lbm.EOS_CS, **w["eos"])
+        rl, rv = lbm.lbm_coexistence(eos)
+        eos.rho_wall = rv
+        lat = lbm.Lattice(w["nx"], w["ny"], w["tau"], lbm.MOD_B, circles=[w["cyl"]], eos=eos)
+        lat.init_droplet(*w["drop"], rl, rv)
+        lat.step(total)
+        rho64 = lat.fields()[0]
+        lat.close()
+        m = np.isfinite(rho64)
+        d = np.abs(rho_b[m] - rho64[m])
+        acc.append({"lattice": w["name"], "side": w["nx"],
+                    "rho_normwise": float("%.3e" % (d.max() / np.max(rho64[m])))})
     b.close()
     value = info["fluid_nodes"] * steps / (ms * 1e-3) / 1e6
     base_nodes, base_ms = 0, 0.0
@@ -613,6 +636,12 @@ def batched_measure(n_domains, precision, steps, warmup, base_count=16):
                                   "boundary_and_advance": round(split[2] / 5, 4)},
             "plain_fp64_loop_mlups": round(base, 1),
             "speedup_vs_plain_fp64_loop": round(value / base, 2),
+            "accuracy_vs_fp64_alone": {
+                "lattices": len(acc), "steps": total,
+                "max_rho_normwise": max((a["rho_normwise"] for a in acc), default=None),
+                "samples": acc,
+                "how": "finite batched lattices (this storage, in the batch) against the same "
+                       "lattice run alone with FP64 storage"},
             "clocks": clk.summary()}
 
 
