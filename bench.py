@@ -590,8 +590,11 @@ def batched_measure(n_domains, precision, steps, warmup, base_count=16, accuracy
     # alone with FP64 storage for the same number of steps
     total = warmup + steps + 5
     acc = []
-    for k in range(0, len(ws), max(1, len(ws) // accuracy_sample) if accuracy_sample else len(ws) + 1):
-        if len(acc) >= accuracy_sample or ws[k]["name"] in unstable:
+    stride = max(1, len(ws) // max(1, accuracy_sample))
+    for k in sorted(range(len(ws)), key=lambda i: (i % stride, i)):  # 0, s, 2s, .., then 1, s+1, ..
+        if len(acc) >= accuracy_sample:
+            break
+        if ws[k]["name"] in unstable:
             continue
         rho_b = b.fields(slots[k])[0]
         w = ws[k]
