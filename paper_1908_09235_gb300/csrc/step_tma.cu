@@ -311,6 +311,40 @@ bool make_ring_tensor_maps_fp16(void* map0, void* map1, const void* base, int nx
   return r == CUDA_SUCCESS;
 }
 
+// A tiled tensor map over a dense array of dims[0] x dims[1] (x dims[2]) elements of esize
+// bytes, row-major with dims[0] innermost, box box[0] x box[1] (x box[2]).
+bool encode_box(void* map, CUtensorMapDataType type, int esize, int rank, const void* base,
+                const cuuint64_t* dims, const cuuint32_t* box) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t strides[2] = {dims[0] * (cuuint64_t)esize,
+                                 dims[0] * dims[1] * (cuuint64_t)esize};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(static_cast<CUtensorMap*>(map), type, rank, const_cast<void*>(base), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Tensor maps of one lattice whose box is a whole tile of the vector step kernel (tw x vh nodes,
+// every plane), for L2 prefetches: FP32 deviations map0 dims (nx, ny, 9); FP16 deviations map0
+// the FP32 rest plane (nx, ny) and map1 the eight FP16 planes (nx, ny, 8; nx % 8 == 0).
+bool make_tile_prefetch_maps(void* map0, void* map1, const void* base, int nx, int ny, int tw,
+                             int vh, bool fp16) {
+  const cuuint64_t d3[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+  if (!fp16) {
+    const cuuint32_t b[3] = {(cuuint32_t)tw, (cuuint32_t)vh, 9};
+    return encode_box(map0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 3, base, d3, b);
+  }
+  if (nx % 8 != 0) return false;
+  const cuuint32_t b0[2] = {(cuuint32_t)tw, (cuuint32_t)vh};
+  if (!encode_box(map0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2, base, d3, b0)) return false;
+  const cuuint64_t d1[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 8};
+  const cuuint32_t b1[3] = {(cuuint32_t)tw, (cuuint32_t)vh, 8};
+  const void* moving = static_cast<const char*>(base) + (size_t)nx * ny * 4;
+  return encode_box(map1, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, 3, moving, d1, b1);
+}
+
 // Tensor map of one FP32 lattice: dims (nx, ny, 9), box 40 x 34 x 9.
 bool make_lattice_tensor_map(void* map, const void* base, int nx, int ny) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();

@@ -11,7 +11,9 @@
 // ring around the tile (the rows above and below, one column on each side) comes from
 // populations staged in shared memory, which needs no registers and fetches the side columns as
 // aligned vectors instead of single-element loads: the two rows by tensor copies where the tile
-// allows (TR), otherwise, and the side columns always, by cp.async.
+// allows (TR), otherwise, and the side columns always, by cp.async.  With TR the FP32 kernel
+// also prefetches into L2, by one tensor-copy prefetch, the tile that a CTA launched one wave
+// of SMs later will load.
 //
 // Streaming is push (f*_a of node x goes to x + e_a of the destination lattice, into solid nodes
 // too, whose slots then hold the outgoing populations the wall pass reads).  A population moving
@@ -63,6 +65,9 @@ struct Vec<float> {
   static constexpr int VH = 8;  // warps per CTA = rows per tile
   static constexpr int kBlocks = 3;
   static constexpr bool kOwnFirst = true;  // issue order of the loads (step_vec_kernel)
+  // L2 prefetch of the tile this many CTAs later in launch order (one CTA per SM ahead): 206 us
+  // against 209 us at 4096^2 (48 ahead: 207, 228: 207, 456: 215, 912: 251)
+  static constexpr int kPrefetchAhead = 152;
   // a staged ring row: 9 planes of SWE elements (x0 - V .. x0 + 32 V + V - 1), plane a at
   // ring_off(a); a tensor copy brings kTmaWidth columns from x0 - kTmaLeft
   static constexpr int SWE = VW * V + 2 * V;
@@ -105,6 +110,7 @@ struct Vec<double> {
   static constexpr int VH = 8;
   static constexpr int kBlocks = 2;
   static constexpr bool kOwnFirst = false;
+  static constexpr int kPrefetchAhead = 0;
   static constexpr int SWE = VW * V + 2 * V;
   static constexpr int kTmaLeft = V, kTmaWidth = SWE;
   template <bool TMA>
@@ -150,6 +156,7 @@ struct Vec<__half> {
   static constexpr int VH = 12;
   static constexpr int kBlocks = 2;
   static constexpr bool kOwnFirst = false;
+  static constexpr int kPrefetchAhead = 0;  // slower with it (152 or 304 ahead: 195 against 187 us)
   // a staged ring row (ring_off(a): element x0 - V of plane a).  Staged by cp.async: 9 plane
   // regions of SWE 4-byte slots.  Staged by tensor copies (TMA): the FP32 rest plane (SWE
   // floats from x0 - V) at 0, then the eight FP16 planes densely, kTmaWidth halves each from
@@ -247,7 +254,9 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
                     const uint8_t* __restrict__ flags, double* __restrict__ rho_m,
                     double* __restrict__ ux_m, double* __restrict__ uy_m,
                     const __grid_constant__ CUtensorMap rmap,
-                    const __grid_constant__ CUtensorMap rmap2, int* __restrict__ err) {
+                    const __grid_constant__ CUtensorMap rmap2,
+                    const __grid_constant__ CUtensorMap pmap,
+                    const __grid_constant__ CUtensorMap pmap2, int* __restrict__ err) {
   using C = typename Pop<S>::C;
   using VT = Vec<S>;
   constexpr int V = VT::V;
@@ -273,6 +282,20 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
   const int lane = threadIdx.x, w = threadIdx.y, tid = w * VW + lane;
   const int nx = p.nx, ny = p.ny, N = p.N;
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * VH;
+  if constexpr (TR && PSI && VT::kPrefetchAhead > 0) {
+    // the populations of the tile kPrefetchAhead CTAs later in launch order go to L2 now (one
+    // box of tensor-copy prefetch), so that its loads find them there
+    const int t = blockIdx.y * gridDim.x + blockIdx.x + VT::kPrefetchAhead;
+    if (tid == 32 && t < gridDim.x * gridDim.y) {
+      const int px = (t % gridDim.x) * TW, py = (t / gridDim.x) * VH;
+      if constexpr (sizeof(S) == 2) {
+        tma::tma_prefetch_2d(&pmap, px, py);
+        tma::tma_prefetch_3d(&pmap2, px, py, 0);
+      } else {
+        tma::tma_prefetch_3d(&pmap, px, py, 0);
+      }
+    }
+  }
   const int nv = min(VW, (nx - x0) / V);  // vectors of this tile inside the lattice
   const Consts<C>& k = p.k<C>();
   const C rho_ref = DEV ? k.rho_ref : C(0);
@@ -619,28 +642,32 @@ cudaError_t launch_vec_t(const DevParams& p, const void* fa, void* fb, const uin
   constexpr int TW = VW * Vec<S>::V, VH = Vec<S>::VH;
   dim3 block(VW, VH);
   dim3 grid((p.nx + TW - 1) / TW, (p.ny + VH - 1) / VH);
-  CUtensorMap map{}, map2{};  // unused by the kernels without tensor copies
+  // ring-row and tile-prefetch maps; unused by the kernels without tensor copies
+  CUtensorMap map{}, map2{}, pmap{}, pmap2{};
   if constexpr (!std::is_same<S, double>::value && EOS != LBM_EOS_NONE) {
+    constexpr bool fp16 = std::is_same<S, __half>::value;
     bool maps = tma_ring && !fields_only && err;
     if (maps) {
-      if constexpr (std::is_same<S, float>::value)
-        maps = make_ring_tensor_map(&map, fa, p.nx, p.ny, Vec<S>::kTmaWidth);
-      else
+      if constexpr (fp16)
         maps = make_ring_tensor_maps_fp16(&map, &map2, fa, p.nx, p.ny, Vec<S>::SWE,
                                           Vec<S>::kTmaWidth);
+      else
+        maps = make_ring_tensor_map(&map, fa, p.nx, p.ny, Vec<S>::kTmaWidth);
+      if (Vec<S>::kPrefetchAhead > 0)
+        maps = maps && make_tile_prefetch_maps(&pmap, &pmap2, fa, p.nx, p.ny, TW, VH, fp16);
     }
     if (maps) {
-      step_vec_kernel<S, EOS, false, true>
-          <<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, err);
+      step_vec_kernel<S, EOS, false, true><<<grid, block, 0, s>>>(
+          p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, pmap, pmap2, err);
       return cudaGetLastError();
     }
   }
   if (fields_only)
-    step_vec_kernel<S, EOS, true, false>
-        <<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, err);
+    step_vec_kernel<S, EOS, true, false><<<grid, block, 0, s>>>(
+        p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, pmap, pmap2, err);
   else
-    step_vec_kernel<S, EOS, false, false>
-        <<<grid, block, 0, s>>>(p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, err);
+    step_vec_kernel<S, EOS, false, false><<<grid, block, 0, s>>>(
+        p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, pmap, pmap2, err);
   return cudaGetLastError();
 }
 
