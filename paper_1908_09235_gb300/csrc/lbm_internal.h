@@ -200,6 +200,7 @@ bool make_ring_tensor_maps_fp16(void* map0, void* map1, const void* base, int nx
                                 int w1);
 bool make_tile_prefetch_maps(void* map0, void* map1, const void* base, int nx, int ny, int tw,
                              int vh, bool fp16);
+bool make_flags_prefetch_map(void* map, const uint8_t* flags, int nx, int ny, int tw, int vh);
 bool make_flags_tensor_map(void* map, const void* base, int nx, int ny);
 cudaError_t launch_step_tma(const void* map, const void* flag_map, const DevParams& p,
                             const void* fa, void* fb, const uint8_t* flags, double* rho_m,

@@ -345,6 +345,15 @@ bool make_tile_prefetch_maps(void* map0, void* map1, const void* base, int nx, i
   return encode_box(map1, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, 3, moving, d1, b1);
 }
 
+// Tensor map of a lattice's node flags (dims (nx, ny) bytes) whose box is a whole tile of the
+// vector step kernel (tw x vh), for L2 prefetches; the row pitch must be a multiple of 16 bytes.
+bool make_flags_prefetch_map(void* map, const uint8_t* flags, int nx, int ny, int tw, int vh) {
+  if (nx % 16 != 0) return false;
+  const cuuint64_t d[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  const cuuint32_t b[2] = {(cuuint32_t)tw, (cuuint32_t)vh};
+  return encode_box(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, 2, flags, d, b);
+}
+
 // Tensor map of one FP32 lattice: dims (nx, ny, 9), box 40 x 34 x 9.
 bool make_lattice_tensor_map(void* map, const void* base, int nx, int ny) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();

@@ -12,8 +12,8 @@
 // populations staged in shared memory, which needs no registers and fetches the side columns as
 // aligned vectors instead of single-element loads: the two rows by tensor copies where the tile
 // allows (TR), otherwise, and the side columns always, by cp.async.  With TR the FP32 kernel
-// also prefetches into L2, by one tensor-copy prefetch, the tile that a CTA launched one wave
-// of SMs later will load.
+// also prefetches into L2, by tensor-copy prefetches, the populations and flags of the tile that
+// the CTA launched one CTA per SM later will load.
 //
 // Streaming is push (f*_a of node x goes to x + e_a of the destination lattice, into solid nodes
 // too, whose slots then hold the outgoing populations the wall pass reads).  A population moving
@@ -65,9 +65,11 @@ struct Vec<float> {
   static constexpr int VH = 8;  // warps per CTA = rows per tile
   static constexpr int kBlocks = 3;
   static constexpr bool kOwnFirst = true;  // issue order of the loads (step_vec_kernel)
-  // L2 prefetch of the tile this many CTAs later in launch order (one CTA per SM ahead): 206 us
-  // against 209 us at 4096^2 (48 ahead: 207, 228: 207, 456: 215, 912: 251)
+  // L2 prefetch of the populations and the flags of the tile this many CTAs later in launch
+  // order (one CTA per SM ahead): 200 us against 209 us at 4096^2 (populations alone: 206 us; 48
+  // ahead: 207, 228: 207, 456: 215, 912: 251; flags 76 or 304 ahead: no better)
   static constexpr int kPrefetchAhead = 152;
+  static constexpr bool kPrefetchPops = true, kPrefetchFlags = true;
   // a staged ring row: 9 planes of SWE elements (x0 - V .. x0 + 32 V + V - 1), plane a at
   // ring_off(a); a tensor copy brings kTmaWidth columns from x0 - kTmaLeft
   static constexpr int SWE = VW * V + 2 * V;
@@ -111,6 +113,7 @@ struct Vec<double> {
   static constexpr int kBlocks = 2;
   static constexpr bool kOwnFirst = false;
   static constexpr int kPrefetchAhead = 0;
+  static constexpr bool kPrefetchPops = false, kPrefetchFlags = false;
   static constexpr int SWE = VW * V + 2 * V;
   static constexpr int kTmaLeft = V, kTmaWidth = SWE;
   template <bool TMA>
@@ -156,7 +159,10 @@ struct Vec<__half> {
   static constexpr int VH = 12;
   static constexpr int kBlocks = 2;
   static constexpr bool kOwnFirst = false;
-  static constexpr int kPrefetchAhead = 0;  // slower with it (152 or 304 ahead: 195 against 187 us)
+  // slower with prefetches (populations 152 or 304 ahead: 195 against 187 us; flags alone 152 or
+  // 304 ahead: 194 us)
+  static constexpr int kPrefetchAhead = 0;
+  static constexpr bool kPrefetchPops = false, kPrefetchFlags = false;
   // a staged ring row (ring_off(a): element x0 - V of plane a).  Staged by cp.async: 9 plane
   // regions of SWE 4-byte slots.  Staged by tensor copies (TMA): the FP32 rest plane (SWE
   // floats from x0 - V) at 0, then the eight FP16 planes densely, kTmaWidth halves each from
@@ -256,7 +262,9 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
                     const __grid_constant__ CUtensorMap rmap,
                     const __grid_constant__ CUtensorMap rmap2,
                     const __grid_constant__ CUtensorMap pmap,
-                    const __grid_constant__ CUtensorMap pmap2, int* __restrict__ err) {
+                    const __grid_constant__ CUtensorMap pmap2,
+                    const __grid_constant__ CUtensorMap fmap, int pf_flags,
+                    int* __restrict__ err) {
   using C = typename Pop<S>::C;
   using VT = Vec<S>;
   constexpr int V = VT::V;
@@ -282,17 +290,22 @@ __global__ void __launch_bounds__(VW* Vec<S>::VH, Vec<S>::kBlocks)
   const int lane = threadIdx.x, w = threadIdx.y, tid = w * VW + lane;
   const int nx = p.nx, ny = p.ny, N = p.N;
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * VH;
-  if constexpr (TR && PSI && VT::kPrefetchAhead > 0) {
-    // the populations of the tile kPrefetchAhead CTAs later in launch order go to L2 now (one
-    // box of tensor-copy prefetch), so that its loads find them there
+  if constexpr (TR && PSI && (VT::kPrefetchPops || VT::kPrefetchFlags)) {
+    // the populations and flags of the tile kPrefetchAhead CTAs later in launch order go to L2
+    // now, by tensor-copy prefetches of one tile-sized box each, so that its loads find them there
     const int t = blockIdx.y * gridDim.x + blockIdx.x + VT::kPrefetchAhead;
     if (tid == 32 && t < gridDim.x * gridDim.y) {
       const int px = (t % gridDim.x) * TW, py = (t / gridDim.x) * VH;
-      if constexpr (sizeof(S) == 2) {
-        tma::tma_prefetch_2d(&pmap, px, py);
-        tma::tma_prefetch_3d(&pmap2, px, py, 0);
-      } else {
-        tma::tma_prefetch_3d(&pmap, px, py, 0);
+      if constexpr (VT::kPrefetchPops) {
+        if constexpr (sizeof(S) == 2) {
+          tma::tma_prefetch_2d(&pmap, px, py);
+          tma::tma_prefetch_3d(&pmap2, px, py, 0);
+        } else {
+          tma::tma_prefetch_3d(&pmap, px, py, 0);
+        }
+      }
+      if constexpr (VT::kPrefetchFlags) {
+        if (pf_flags) tma::tma_prefetch_2d(&fmap, px, py);
       }
     }
   }
@@ -643,7 +656,8 @@ cudaError_t launch_vec_t(const DevParams& p, const void* fa, void* fb, const uin
   dim3 block(VW, VH);
   dim3 grid((p.nx + TW - 1) / TW, (p.ny + VH - 1) / VH);
   // ring-row and tile-prefetch maps; unused by the kernels without tensor copies
-  CUtensorMap map{}, map2{}, pmap{}, pmap2{};
+  CUtensorMap map{}, map2{}, pmap{}, pmap2{}, fmap{};
+  int pf_flags = 0;  // fmap valid (row pitch of the flags a multiple of 16 bytes)
   if constexpr (!std::is_same<S, double>::value && EOS != LBM_EOS_NONE) {
     constexpr bool fp16 = std::is_same<S, __half>::value;
     bool maps = tma_ring && !fields_only && err;
@@ -653,21 +667,23 @@ cudaError_t launch_vec_t(const DevParams& p, const void* fa, void* fb, const uin
                                           Vec<S>::kTmaWidth);
       else
         maps = make_ring_tensor_map(&map, fa, p.nx, p.ny, Vec<S>::kTmaWidth);
-      if (Vec<S>::kPrefetchAhead > 0)
+      if (Vec<S>::kPrefetchPops)
         maps = maps && make_tile_prefetch_maps(&pmap, &pmap2, fa, p.nx, p.ny, TW, VH, fp16);
+      if (maps && Vec<S>::kPrefetchFlags)
+        pf_flags = make_flags_prefetch_map(&fmap, flags, p.nx, p.ny, TW, VH) ? 1 : 0;
     }
     if (maps) {
       step_vec_kernel<S, EOS, false, true><<<grid, block, 0, s>>>(
-          p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, pmap, pmap2, err);
+          p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, pmap, pmap2, fmap, pf_flags, err);
       return cudaGetLastError();
     }
   }
   if (fields_only)
     step_vec_kernel<S, EOS, true, false><<<grid, block, 0, s>>>(
-        p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, pmap, pmap2, err);
+        p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, pmap, pmap2, fmap, 0, err);
   else
     step_vec_kernel<S, EOS, false, false><<<grid, block, 0, s>>>(
-        p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, pmap, pmap2, err);
+        p, fa, fb, flags, rho_m, ux_m, uy_m, map, map2, pmap, pmap2, fmap, 0, err);
   return cudaGetLastError();
 }
 
