@@ -303,9 +303,12 @@ def test_vector_step_equals_scalar_tiles(gpu_lib, precision, shape):
 # 512 and 516 wide hold tiles copied by TMA (x0 - 4 >= 0, x0 + 132 <= nx) beside seam tiles and,
 # at 516, a last tile one vector wide, which stage by cp.async; 256 wide has seam tiles only.
 # FP16 (x0 - 8 >= 0, x0 + 136 <= nx, nx % 8 == 0): 512 and 520 mix both kinds of tile; 516 is
-# not a multiple of 8, so every tile stages by cp.async.
+# not a multiple of 8, so every tile stages by cp.async.  FP32 grids of more than 152 CTAs also
+# prefetch the tile 152 CTAs ahead into L2: 1024 x 320 with its flags, 1028 x 320 (a flag row
+# pitch that no tensor map can describe) without them.
 @pytest.mark.parametrize("precision,shape", [
     (lbm.FP32_DEV, (512, 64)), (lbm.FP32_DEV, (516, 40)), (lbm.FP32_DEV, (256, 192)),
+    (lbm.FP32_DEV, (1024, 320)), (lbm.FP32_DEV, (1028, 320)),
     (lbm.FP16_DEV, (512, 64)), (lbm.FP16_DEV, (520, 40)), (lbm.FP16_DEV, (516, 40))])
 def test_tma_ring_step_equals_scalar_tiles(gpu_lib, precision, shape):
     nx, ny = shape
