@@ -86,14 +86,21 @@ __global__ void init_eq_kernel(DevParams p, const uint8_t* __restrict__ flags,
       for (int a = 0; a < 9; ++a) Pop<S>::store(f, a, N, n, C(0));
       continue;
     }
+    // Eq. (4), f_eq = w rho (A + 3 e.u + 4.5 (e.u)^2) with A = 1 - 1.5 u.u, in FP64 (the FP64
+    // pipe bounds this kernel): opposite directions share w rho (A + 4.5 (e.u)^2) and differ in
+    // the sign of 3 w rho e.u; the deviation formats take w rho_ref off the shared part
     const double r = rho[n], u = ux[n], v = uy[n];
-    const double uu = u * u + v * v;
+    const double A = 1.0 - 1.5 * (u * u + v * v);
+    const double ref = Pop<S>::dev ? p.rho_ref : 0.0;
+    Pop<S>::store(f, 0, N, n, C(wgt<double>(0) * (r * A - ref)));
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      const double eu = ex(a) * u + ey(a) * v;
-      double fe = wgt<double>(a) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);  // Eq. (4)
-      if (Pop<S>::dev) fe -= wgt<double>(a) * p.rho_ref;
-      Pop<S>::store(f, a, N, n, C(fe));
+    for (int i = 0; i < 4; ++i) {
+      const int a = i == 0 ? 1 : (i == 1 ? 2 : (i == 2 ? 5 : 6));  // e_a = (1,0) (0,1) (1,1) (-1,1)
+      const double eu = i == 0 ? u : (i == 1 ? v : (i == 2 ? u + v : v - u));
+      const double w = wgt<double>(a);
+      const double P = w * (r * (A + 4.5 * eu * eu) - ref), Q = 3.0 * w * r * eu;
+      Pop<S>::store(f, a, N, n, C(P + Q));
+      Pop<S>::store(f, opposite(a), N, n, C(P - Q));
     }
   }
 }
