@@ -200,11 +200,11 @@ def time_variant(w, scheme, precision, steps, warmup):
     return ms_step, ms_bnd, ms_total, info
 
 
-def cpu_oracle_rate(w, budget_s, max_steps, openmp=False):
+def cpu_oracle_rate(w, budget_s, max_steps, openmp=False, warmup=0):
     """The FP64 CPU oracle on the same lattice, as many steps as fit the budget: the serial
     build (one thread) or the -fopenmp build of the same source (all host cores; falls back to
-    the serial build where -fopenmp does not compile).  Returns (MLUPS, steps, seconds,
-    threads)."""
+    the serial build where -fopenmp does not compile), after up to `warmup` untimed steps (also
+    within the budget).  Returns (MLUPS, steps, seconds, threads, warm-up steps done)."""
     import oracle as O
     if openmp:
         try:
@@ -219,6 +219,10 @@ def cpu_oracle_rate(w, budget_s, max_steps, openmp=False):
                     openmp=openmp)
     s.init_droplet(*w.drop, rl, rv)
     n_fluid = int((s.flags() & 1 == 0).sum())
+    warm, t0 = 0, time.perf_counter()
+    while warm < warmup and time.perf_counter() - t0 < budget_s / 2:
+        s.step(1)
+        warm += 1
     done, t0 = 0, time.perf_counter()
     while done < max_steps:
         s.step(1)
@@ -226,7 +230,7 @@ def cpu_oracle_rate(w, budget_s, max_steps, openmp=False):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return n_fluid * done / dt / 1e6, done, dt, O.num_threads(openmp)
+    return n_fluid * done / dt / 1e6, done, dt, O.num_threads(openmp), warm
 
 
 def run_reference(args, w):
@@ -235,10 +239,10 @@ def run_reference(args, w):
     if rank != 0:
         return
     budget = min(150.0, max(10.0, 3.0 * args.steps))  # a bounded sample: a few minutes at most
-    mlups, done, dt, cores = cpu_oracle_rate(w, budget_s=budget, max_steps=args.steps,
-                                             openmp=True)
+    mlups, done, dt, cores, warm = cpu_oracle_rate(w, budget_s=budget, max_steps=args.steps,
+                                                   openmp=True, warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": UNIT,
-            "n_gpus": 0, "steps": done, "warmup": 0, "ms_per_step": round(1e3 * dt / done, 3),
+            "n_gpus": 0, "steps": done, "warmup": warm, "ms_per_step": round(1e3 * dt / done, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "scheme": "mod_b"},
             "cpu_baseline": {"value": round(mlups, 3), "unit": UNIT, "cores": cores,
@@ -943,11 +947,12 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mlups, done, dt, cores = cpu_oracle_rate(w, budget_s=15.0, max_steps=50)
+        mlups, done, dt, cores, _ = cpu_oracle_rate(w, budget_s=15.0, max_steps=50)
         cpu = {"value": round(mlups, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d FP64 time steps of the %dx%d lattice, scheme B (%.1f s), serial build"
                          % (done, w.nx, w.ny, dt)}
-        mlups, done, dt, cores = cpu_oracle_rate(w, budget_s=15.0, max_steps=200, openmp=True)
+        mlups, done, dt, cores, _ = cpu_oracle_rate(w, budget_s=15.0, max_steps=200,
+                                                    openmp=True)
         cpu["all_cores"] = {"value": round(mlups, 3), "unit": UNIT, "cores": cores,
                             "kind": "oracle, -fopenmp build of the same source",
                             "sample": "%d FP64 time steps of the %dx%d lattice (%.1f s)"
@@ -955,7 +960,7 @@ def main():
         # the small parity case, 1000 steps: the serial oracle and the GPU (FP64, through lbm_step)
         from paper_1908_09235_gb300 import workloads
         sw = workloads.SMALL
-        o_mlups, o_done, o_dt, _ = cpu_oracle_rate(sw, budget_s=15.0, max_steps=1000)
+        o_mlups, o_done, o_dt, _, _ = cpu_oracle_rate(sw, budget_s=15.0, max_steps=1000)
         slat, _ = make_lattice(sw, lbm.MOD_B, lbm.FP64)
         slat.step(32)
         torch.cuda.synchronize()
