@@ -5,7 +5,8 @@
 // Each lane owns V consecutive nodes of one row and moves every population plane as one vector
 // (FP32: 4 x 4 B, FP64: 2 x 8 B = 128-bit accesses; FP16 deviations: the FP32 rest plane as
 // 4 x 4 B and each FP16 plane as 4 x 2 B), so a warp reads or writes 32 V nodes of a plane with
-// one request.  A CTA of 8 warps covers a (32 V) x 8 tile, one row per warp.
+// one request.  A CTA of VH warps covers a (32 V) x VH tile, one row per warp (VH = 8; 12 for
+// the FP16 format).
 //
 // psi stencil: psi of the tile's own nodes comes from the lanes' registers; psi of the one-node
 // ring around the tile (the rows above and below, one column on each side) comes from
@@ -13,7 +14,7 @@
 // aligned vectors instead of single-element loads: the two rows by tensor copies where the tile
 // allows (TR), otherwise, and the side columns always, by cp.async.  With TR the FP32 kernel
 // also prefetches into L2, by tensor-copy prefetches, the populations and flags of the tile that
-// the CTA launched one CTA per SM later will load.
+// the CTA launched 152 CTAs later (one per SM of GB300) will load.
 //
 // Streaming is push (f*_a of node x goes to x + e_a of the destination lattice, into solid nodes
 // too, whose slots then hold the outgoing populations the wall pass reads).  A population moving
