@@ -4,6 +4,8 @@ Each test names its source: a value the paper prints, an exact conservation prop
 states for a scheme, a closed-form flow solution derived here, or an ordering the paper reports.
 """
 import math
+import os
+import sys
 
 import numpy as np
 import pytest
@@ -20,16 +22,35 @@ def _cs():
     return T, rl, rv
 
 
+def _golden(name):
+    """Rows of a fixture under tests/golden/ (values the paper prints; comments name where)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    with open(path) as f:
+        return [ln.split("#")[0].strip() for ln in f if ln.split("#")[0].strip()]
+
+
 # --- Sec. 3.2: exponential psi with |G| = 10/3 gives rho_L ~ 2.783, rho_V ~ 0.3675 -----------
 def test_flat_interface_exponential_printed_densities():
+    printed = dict((k, float(v)) for k, v in (ln.split() for ln in _golden(
+        "exp_psi_coexistence.txt")))
     nx, ny = 4, 128
     s = O.OracleSim(nx, ny, 1.0, eos=O.EOS_EXP, G=-10.0 / 3.0, psi0=1.0, rho0=1.0)
     y = np.arange(ny)
     s.init_fields(np.tile(np.where(np.abs(y - ny / 2) < ny / 4, 2.7, 0.4)[:, None], (1, nx)))
     s.step(6000)
     rho, _, _ = s.fields()
-    assert rho.max() == pytest.approx(2.783, rel=0.01)
-    assert rho.min() == pytest.approx(0.3675, rel=0.01)
+    assert rho.max() == pytest.approx(printed["rho_L"], rel=0.01)
+    assert rho.min() == pytest.approx(printed["rho_V"], rel=0.01)
+
+
+def test_bench_table1_is_the_printed_table():
+    # the cylinder-flow comparison of bench.py quotes Table 1 (Sec. 5.1) as printed
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    rows = [[c.strip() for c in ln.split("|")] for ln in _golden("table1_cylinder_flow.txt")]
+    assert len(rows) == sum(len(v) for v in bench.TABLE1.values())
+    for src, re_, l, th, cd in rows:
+        assert bench.TABLE1[int(re_)][src] == (float(l), float(th), float(cd))
 
 
 def test_sign_of_G_spinodal():
