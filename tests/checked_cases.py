@@ -12,7 +12,9 @@ import numpy as np
 
 from paper_1908_09235_gb300 import lbm, workloads
 
-SHAPES = [(256, 192), (100, 100), (132, 68), (16, 12), (4, 130), (130, 4), (5, 6)]
+# 1040 x 256: vector-kernel tiles whose psi ring rows come by tensor copies (FP32 and FP16) and,
+# for FP32, more than 152 CTAs, so the L2 prefetches of later tiles (with the flags map) run too
+SHAPES = [(256, 192), (100, 100), (132, 68), (16, 12), (4, 130), (130, 4), (5, 6), (1040, 256)]
 SCHEMES = [lbm.MOD_B, lbm.BOUZIDI_Q, lbm.ZHAO_YONG, lbm.HBB]
 STEPS = 20
 
