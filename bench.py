@@ -397,6 +397,55 @@ def run_cylinder_flow(args):
                       "runs": runs}), flush=True)
 
 
+# Sec. 3.2 (Figs. 8 and 11): what the paper states about the mass of its droplet-on-cylinder run
+PAPER_MASS = {"zhao_yong": "about 40% of the mass lost after 1500 steps (Fig. 8)",
+              "mod_a": "maximum variation of the normalised mass about 0.01% (Fig. 11)",
+              "mod_b": "maximum variation of the normalised mass about 0.01% (Fig. 11)"}
+
+
+def run_paper_mass(args):
+    """The paper's own two-phase test (Sec. 3.2): a 300 x 350 periodic lattice, a cylinder of
+    radius 70 at (150, 130), a droplet of radius 50 on its top (tanh profile, width 5, the
+    printed coexistence densities), the exponential pseudopotential with |G| = 10/3 (attractive,
+    reading r1), nu = 0.15 (tau = 0.95), virtual wall density 1.5; every curved-wall scheme in
+    the storage format of --precision (FP64 for the comparison with the paper), the normalised
+    mass m/m0 after each chunk of steps (Figs. 8 and 11), beside what the paper states."""
+    import torch
+
+    from paper_1908_09235_gb300 import lbm
+    torch.cuda.set_device(0)
+    marks = (100, 500, 1000, 1500, 2000, 5000, 10000, 20000, 40000, 60000)
+    marks = tuple(m for m in marks if m <= args.mass_steps)
+    runs = []
+    for name in ("hbb", "fh", "mls", "bouzidi_l", "bouzidi_q", "zhao_yong", "mod_a", "mod_b",
+                 "bao"):
+        eos = lbm.make_eos(lbm.EOS_EXP, G=-10.0 / 3.0, psi0=1.0, rho0=1.0, rho_wall=1.5)
+        lat = lbm.Lattice(300, 350, 0.95, lbm.SCHEMES[name], circles=[(150.0, 130.0, 70.0)],
+                          eos=eos, precision=lbm.PRECISIONS[args.precision])
+        lat.init_droplet(150.0, 200.0, 50.0, 5.0, 2.783, 0.3675)
+        m0 = lat.mass()
+        done, curve, status, dev = 0, {}, "ok", 0.0
+        t0 = time.perf_counter()
+        for m in marks:
+            lat.step(m - done)
+            done = m
+            try:
+                r = lat.mass() / m0
+            except lbm.LBMError as e:
+                status = "unstable (status %d) before step %d" % (e.status, m)
+                break
+            curve[str(m)] = float("%.9f" % r)
+            dev = max(dev, abs(r - 1.0))
+        wall = time.perf_counter() - t0
+        lat.close()
+        runs.append({"scheme": name, "status": status, "mass_over_m0": curve,
+                     "max_abs_mass_variation": float("%.3e" % dev),
+                     "seconds": round(wall, 2), "paper": PAPER_MASS.get(name)})
+    print(json.dumps({"report": "droplet on a cylinder, mass over time (Sec. 3.2, Figs. 8, 11)",
+                      "domain": [300, 350], "tau": 0.95, "storage": args.precision,
+                      "runs": runs}), flush=True)
+
+
 def _field_errors(got, ref):
     import numpy as np
     m = np.isfinite(ref[0])
@@ -825,6 +874,9 @@ def main():
     ap.add_argument("--batch-domains", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000,
                     help="batched workload: timed steps of every lattice")
+    ap.add_argument("--paper-mass", action="store_true",
+                    help="Sec. 3.2: mass over time of the paper's droplet on a cylinder, every scheme")
+    ap.add_argument("--mass-steps", type=int, default=60000)
     ap.add_argument("--cylinder-flow", action="store_true",
                     help="Sec. 5.1: flow past a cylinder at Re 20 and 40 against Table 1")
     ap.add_argument("--cyl-diameter", type=int, default=40)
@@ -867,6 +919,8 @@ def main():
         return run_precision_report(args)
     if args.cylinder_flow:
         return run_cylinder_flow(args)
+    if args.paper_mass:
+        return run_paper_mass(args)
 
     import torch
     world, rank, local = dist_setup()
