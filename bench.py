@@ -294,7 +294,7 @@ def run_e2e(w, steps):
     return info["n_fluid"] * steps / dt / 1e6, 24 * n / steps, 24 * n / steps, split
 
 
-# Table 1 of the paper (Sec. 5.1): 2L/D, separation angle (degrees), drag coefficient
+# Table 1 of the paper (Sec. 4.2): 2L/D, separation angle (degrees), drag coefficient
 TABLE1 = {20: {"scheme A": (1.90, 41.35, 2.130), "scheme B": (1.91, 41.56, 2.133),
                "Dennis and Chang 1970": (1.88, 43.7, 2.045)},
           40: {"scheme A": (4.61, 53.93, 1.590), "scheme B": (4.64, 53.93, 1.593),
@@ -348,7 +348,7 @@ def cylinder_wake(ux, uy, cx, cy, r, D):
 
 
 def run_cylinder_flow(args):
-    """Steady flow past a circular cylinder, Sec. 5.1: domain 40 D x 25 D, cylinder of diameter
+    """Steady flow past a circular cylinder, Sec. 4.2: domain 40 D x 25 D, cylinder of diameter
     D at (15 D, 12.5 D), U0 = 0.1, Zou-He velocity inlet, fully developed outlet, periodic in y,
     Re = U0 D / nu.  Runs each (Re, scheme) until the drag changes by less than 1e-6 (relative)
     over 1000 steps, then reports C_d = F_x / (0.5 rho U0^2 D), 2L/D and the separation angle
@@ -392,7 +392,7 @@ def run_cylinder_flow(args):
                          "theta_s_deg": round(theta, 2),
                          "mlups": round(n_fluid * steps / wall / 1e6, 1),
                          "table1": TABLE1[Re]})
-    print(json.dumps({"report": "steady flow past a circular cylinder (Sec. 5.1, Table 1)",
+    print(json.dumps({"report": "steady flow past a circular cylinder (Sec. 4.2, Table 1)",
                       "D": D, "domain": [nx, ny], "U0": U0, "storage": args.precision,
                       "runs": runs}), flush=True)
 
@@ -878,7 +878,7 @@ def main():
                     help="Sec. 3.2: mass over time of the paper's droplet on a cylinder, every scheme")
     ap.add_argument("--mass-steps", type=int, default=60000)
     ap.add_argument("--cylinder-flow", action="store_true",
-                    help="Sec. 5.1: flow past a cylinder at Re 20 and 40 against Table 1")
+                    help="Sec. 4.2: flow past a cylinder at Re 20 and 40 against Table 1")
     ap.add_argument("--cyl-diameter", type=int, default=40)
     ap.add_argument("--cyl-max-steps", type=int, default=400000)
     ap.add_argument("--precision-report", action="store_true",

@@ -17,7 +17,7 @@
  *
  * Conventions.  Node (i, j) sits at position (i, j) in lattice units, i in [0, nx), j in [0, ny);
  * its linear index is j*nx + i (row-major, y outer).  The outer box is periodic in x and y (x
- * becomes a channel with a velocity inlet and an outlet after lbm_set_inflow, Sec. 5.1).
+ * becomes a channel with a velocity inlet and an outlet after lbm_set_inflow, Sec. 4.2).
  * D2Q9 directions: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
  * All host arrays are caller-owned and are read or written only during the call.  Device state is
  * owned by the context and released by lbm_destroy.  Functions return an lbm_status; a non-zero
@@ -212,7 +212,7 @@ lbm_status lbm_links(lbm_ctx* ctx, int32_t* node, uint8_t* dir, double* q, int64
  * error. */
 lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
 
-/* Channel flow past solid bodies (Sec. 5.1, steady flow past a circular cylinder): from the next
+/* Channel flow past solid bodies (Sec. 4.2, steady flow past a circular cylinder): from the next
  * step on (and with the force recorded for lbm_force), column i = 0 is a velocity inlet with
  * the uniform profile (u_in, 0) imposed by Zou and
  * He's rule for the three populations entering from the left, and column i = nx - 1 is a
@@ -222,13 +222,13 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
  * and later graphs; there is no call to return to a periodic x. */
 lbm_status lbm_set_inflow(lbm_ctx* ctx, double u_in);
 
-/* Force on all solid nodes during the last time step by momentum exchange (Sec. 5.1, after Mei
+/* Force on all solid nodes during the last time step by momentum exchange (Sec. 4.2, after Mei
  * et al. 2002): the sum over cut links of e_a (f*_a(x_b, t) + f_abar(x_b, t+1)), the incoming
  * value being the one the curved-wall scheme wrote, in lattice units (momentum per step).
  * FP64, per boundary node in a fixed lane order, then over boundary nodes in ascending order on
  * the host.  Blocks.  0 before the first recorded step and when there are no cut links.
  * LBM_ESTATE unless the context records the force (lbm_options.track_force or
- * lbm_set_inflow).  The drag coefficient of Sec. 5.1 is fx / (0.5 rho U0^2 D). */
+ * lbm_set_inflow).  The drag coefficient of Sec. 4.2 is fx / (0.5 rho U0^2 D). */
 lbm_status lbm_force(lbm_ctx* ctx, double* fx, double* fy);
 
 /* ---- Checkpoint and resume ------------------------------------------------------------------

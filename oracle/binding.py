@@ -273,7 +273,7 @@ class OracleSim:
         return self._lib.or_fallbacks(self._s)
 
     def set_inflow(self, u_in):
-        """Channel mode (Sec. 5.1): Zou-He velocity inlet at i = 0, fully developed outlet at
+        """Channel mode (Sec. 4.2): Zou-He velocity inlet at i = 0, fully developed outlet at
         i = nx - 1; single-phase flows."""
         self._lib.or_set_inflow(self._s, float(u_in))
 

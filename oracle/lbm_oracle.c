@@ -47,7 +47,7 @@ struct or_sim {
   double* lq;
   long fallbacks;
   double last_leak, last_max_node_leak;
-  /* channel mode (flow past a cylinder, Sec. 5.1): velocity inlet at i = 0, outlet at nx - 1 */
+  /* channel mode (flow past a cylinder, Sec. 4.2): velocity inlet at i = 0, outlet at nx - 1 */
   int open_x;
   double u_in;
   /* momentum-exchange force on the solid nodes during the last step */
@@ -577,7 +577,7 @@ static void apply_boundary(or_sim* s) {
       s->fn[ab * N + n] = val;
       sum_out += fo;
       sum_in += val;
-      /* Momentum exchange (Sec. 5.1, after Mei et al. 2002): f*_a(x_b) goes into the wall
+      /* Momentum exchange (Sec. 4.2, after Mei et al. 2002): f*_a(x_b) goes into the wall
        * along e_a and f_abar(x_b, t+1) comes back along -e_a, so the wall receives
        * e_a (f*_a + f_abar) through this link. */
       node_fx += EX[a] * (fo + val);
@@ -599,7 +599,7 @@ static void apply_boundary(or_sim* s) {
   s->force_y = force_y;
 }
 
-/* Channel ends (Sec. 5.1), after streaming and the wall schemes.  Inlet i = 0: the populations
+/* Channel ends (Sec. 4.2), after streaming and the wall schemes.  Inlet i = 0: the populations
  * entering from the left (1, 5, 8) follow from the prescribed velocity (u_in, 0) and the known
  * ones by Zou and He's rule (bounce-back of the non-equilibrium part normal to the inlet):
  *   rho = (f0 + f2 + f4 + 2 (f3 + f6 + f7)) / (1 - u_in)

@@ -89,7 +89,7 @@ long or_fallbacks(const or_sim* s);
 /* Threads the per-node loops use: 1 in the serial build, the OpenMP maximum in the -fopenmp
  * build (the same source; test and host-timing infrastructure only). */
 int or_num_threads(void);
-/* Channel mode for the flow past a cylinder (Sec. 5.1): Zou-He velocity inlet (u_in, 0) at
+/* Channel mode for the flow past a cylinder (Sec. 4.2): Zou-He velocity inlet (u_in, 0) at
  * i = 0 and a fully developed outlet at i = nx - 1 (x no longer periodic; y stays periodic).
  * Single-phase flows only (the psi stencil would still wrap in x). */
 void or_set_inflow(or_sim* s, double u_in);

@@ -290,7 +290,7 @@ __device__ __forceinline__ void boundary_group(const DevParams& p, int b, int k,
     in_d = Pop<S>::store_t(L.dst, dst, N, copy ? fo_d : val - wr);
   }
   if (force) {
-    // Momentum exchange (Sec. 5.1, after Mei et al. 2002): through link a the wall receives
+    // Momentum exchange (Sec. 4.2, after Mei et al. 2002): through link a the wall receives
     // e_a (f*_a(x_b, t) + f_abar(x_b, t+1)), with the incoming value as stored; FP64 sums over
     // the node's links in the fixed group order, one (fx, fy) per boundary node.
     const double m = act ? double(fo_d) + double(in_d) + 2.0 * wgt<double>(a) * L.rho_ref : 0.0;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(128) boundary_kernel(DevParams p, int nb,
                     force, 0xffffffffu);
 }
 
-// Channel ends (Sec. 5.1), after streaming and the wall pass; one thread per row j.  Inlet
+// Channel ends (Sec. 4.2), after streaming and the wall pass; one thread per row j.  Inlet
 // i = 0: the populations entering from the left (1, 5, 8) follow from the prescribed velocity
 // (u_in, 0) and the known ones by Zou and He's rule:
 //   rho = (f0 + f2 + f4 + 2 (f3 + f6 + f7)) / (1 - u_in),  f1 = f3 + 2/3 rho u_in,

@@ -446,7 +446,7 @@ class Lattice:
         return lbm_info(self.ctx)
 
     def set_inflow(self, u_in):
-        """Channel mode (Sec. 5.1): velocity inlet (u_in, 0) at x = 0, fully developed outlet."""
+        """Channel mode (Sec. 4.2): velocity inlet (u_in, 0) at x = 0, fully developed outlet."""
         lbm_set_inflow(self.ctx, u_in)
 
     def force(self):

@@ -55,7 +55,7 @@ def run_cases():
                     lat.step(STEPS)
                     out["%dx%d/p%d/k%d/s%d" % (nx, ny, precision, path, scheme)] = _digest(lat)
                     lat.close()
-    # channel ends (Sec. 5.1) with the momentum exchange recorded
+    # channel ends (Sec. 4.2) with the momentum exchange recorded
     for precision in (lbm.FP64, lbm.FP32_DEV, lbm.FP16_DEV):
         lat = lbm.Lattice(64, 20, 0.8, lbm.MOD_B, circles=[(20.3, 9.7, 4.1)],
                           eos=lbm.make_eos(lbm.EOS_NONE), precision=precision)

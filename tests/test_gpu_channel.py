@@ -1,4 +1,4 @@
-"""GPU channel flow past a cylinder (Sec. 5.1 set-up) through the C ABI, against the oracle:
+"""GPU channel flow past a cylinder (Sec. 4.2 set-up) through the C ABI, against the oracle:
 Zou-He velocity inlet, fully developed outlet, curved walls, momentum-exchange force."""
 import numpy as np
 import pytest

@@ -1,4 +1,4 @@
-"""Oracle pins for the flow-past-a-cylinder set-up of Sec. 5.1: the momentum-exchange force on
+"""Oracle pins for the flow-past-a-cylinder set-up of Sec. 4.2: the momentum-exchange force on
 solid bodies and the channel ends (Zou-He velocity inlet, fully developed outlet).
 
 Each pin is a fact fixed by the mathematics, not a restatement of the oracle's code:

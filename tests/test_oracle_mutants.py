@@ -127,7 +127,7 @@ MUTANTS = [
     ("q_far_root", "double t = c->solid_outside ? (-bq + sq) / aa : (-bq - sq) / aa;",
      "double t = c->solid_outside ? (-bq + sq) / aa : (-bq + sq) / aa;",
      "PIN.test_geometry_brute_force(dict(nx=40, ny=36, circles=[(20, 15, 7.0)]))"),
-    # Sec. 5.1 channel: Zou-He inlet and the momentum exchange
+    # Sec. 4.2 channel: Zou-He inlet and the momentum exchange
     ("zou_he_normal_population", "f[1 * N + n] = f3 + 2.0 / 3.0 * rho * u;",
      "f[1 * N + n] = f3 + 1.0 / 3.0 * rho * u;", "CH.test_zou_he_inlet_and_fully_developed_outlet()"),
     ("zou_he_density", "double rho = (f0 + f2 + f4 + 2.0 * (f3 + f6 + f7)) / (1.0 - u);",

@@ -44,7 +44,7 @@ def test_flat_interface_exponential_printed_densities():
 
 
 def test_bench_table1_is_the_printed_table():
-    # the cylinder-flow comparison of bench.py quotes Table 1 (Sec. 5.1) as printed
+    # the cylinder-flow comparison of bench.py quotes Table 1 (Sec. 4.2) as printed
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
     rows = [[c.strip() for c in ln.split("|")] for ln in _golden("table1_cylinder_flow.txt")]
