@@ -446,6 +446,42 @@ def run_paper_mass(args):
                       "runs": runs}), flush=True)
 
 
+def run_paper_gravity(args):
+    """The paper's single-phase leakage test (Sec. 3.1, Figs. 3-5): a 100 x 50 lattice, periodic in
+    x, flat solid walls below and above with the fraction q = 0.1 .. 0.9 on both, tau = 1,
+    gravity (0, -rho g) with g = 0.001, uniform rho = 1 at rest initially; the averaged mass
+    change rate eps = |m - m0| / m0 x 100% after 60000 steps (Fig. 5) for each scheme, in the
+    storage format of --precision (FP64 for the comparison with the paper)."""
+    import numpy as np
+    import torch
+
+    from paper_1908_09235_gb300 import lbm
+    torch.cuda.set_device(0)
+    nx, ny = 100, 50
+    qs = [n / 10 for n in range(1, 10)]
+    table = {}
+    for name in ("mls", "bouzidi_l", "bouzidi_q", "zhao_yong", "mod_a", "mod_b"):
+        row = {}
+        for q in qs:
+            lat = lbm.Lattice(nx, ny, 1.0, lbm.SCHEMES[name], wall_q_lo=q, wall_q_hi=q,
+                              eos=lbm.make_eos(lbm.EOS_NONE, gy=-0.001),
+                              precision=lbm.PRECISIONS[args.precision])
+            lat.init_fields(np.ones(nx * ny))
+            m0 = lat.mass()
+            lat.step(args.gravity_steps)
+            try:
+                row["%.1f" % q] = float("%.4g" % (abs(lat.mass() - m0) / m0 * 100.0))
+            except lbm.LBMError as e:
+                row["%.1f" % q] = "unstable (status %d)" % e.status
+            lat.close()
+        table[name] = row
+    print(json.dumps({"report": "static flow under gravity, averaged mass change rate eps in % "
+                                "(Sec. 3.1, Fig. 5)", "domain": [nx, ny], "tau": 1.0, "g": 0.001,
+                      "steps": args.gravity_steps, "storage": args.precision, "eps": table,
+                      "paper": "Zhao-Yong's eps much larger than the other schemes' at every q; "
+                               "MLS and Bouzidi conserve mass at q = 0.5 only"}), flush=True)
+
+
 def _field_errors(got, ref):
     import numpy as np
     m = np.isfinite(ref[0])
@@ -877,6 +913,9 @@ def main():
     ap.add_argument("--paper-mass", action="store_true",
                     help="Sec. 3.2: mass over time of the paper's droplet on a cylinder, every scheme")
     ap.add_argument("--mass-steps", type=int, default=60000)
+    ap.add_argument("--paper-gravity", action="store_true",
+                    help="Sec. 3.1: mass change rate of static flow under gravity, every q")
+    ap.add_argument("--gravity-steps", type=int, default=60000)
     ap.add_argument("--cylinder-flow", action="store_true",
                     help="Sec. 4.2: flow past a cylinder at Re 20 and 40 against Table 1")
     ap.add_argument("--cyl-diameter", type=int, default=40)
@@ -921,6 +960,8 @@ def main():
         return run_cylinder_flow(args)
     if args.paper_mass:
         return run_paper_mass(args)
+    if args.paper_gravity:
+        return run_paper_gravity(args)
 
     import torch
     world, rank, local = dist_setup()
